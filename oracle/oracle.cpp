@@ -533,8 +533,10 @@ struct Schedule {
 //    distribution stationary either way;
 //  * the minimum energy and its configuration are recorded at the start and
 //    after every colour phase (strict improvement keeps the earliest).
-// The draw for generator j of colour c at sweep t of chain `chain` is lane
-// (j & 3) of Philox(seed; (c<<16)|(j>>2), t, chain_lo, TAG_SA|chain_hi<<8).
+// The draw for the face (a, b) of colour c at sweep t of chain `chain` is lane
+// (ia & 3) of Philox(seed; (c<<16)|(ib<<8)|(ia>>2), t, chain_lo,
+// TAG_SA|chain_hi<<8) with ia = (a+1)>>1 and ib = (b+1)>>1 (distinct within a
+// colour, since a colour fixes the parities of a and b).
 struct ChainResult {
   int32_t best_E;
   int32_t final_E;
@@ -552,7 +554,7 @@ ChainResult anneal_chain(const Code& code, const Noise& n, const Schedule& sch, 
     double beta = beta_at(sch.kind, sch.n_sweeps, sch.beta0, sch.beta1, t);
     for (int colour = 0; colour < 4; ++colour) {
       for (int f = code.colour_start[colour]; f < code.colour_start[colour + 1]; ++f) {
-        int j = f - code.colour_start[colour];
+        const int ia = (code.faces[f].a + 1) >> 1, ib = (code.faces[f].b + 1) >> 1;
         // dE = H(C G_f) - H(C), summed over the support of G_f.
         int64_t dE = 0;
         for (int k = 0; k < 4; ++k) {
@@ -564,9 +566,9 @@ ChainResult anneal_chain(const Code& code, const Noise& n, const Schedule& sch, 
         if (dE <= 0) {
           accept = true;
         } else {
-          Draw4 r = philox4x32_10(seed, ((uint32_t)colour << 16) | (uint32_t)(j >> 2), (uint32_t)t, chain_lo,
-                                  TAG_SA | (chain_hi << 8));
-          accept = r.v[j & 3] < accept_threshold(beta, (int32_t)dE, n.scale);
+          Draw4 r = philox4x32_10(seed, ((uint32_t)colour << 16) | ((uint32_t)ib << 8) | (uint32_t)(ia >> 2),
+                                  (uint32_t)t, chain_lo, TAG_SA | (chain_hi << 8));
+          accept = r.v[ia & 3] < accept_threshold(beta, (int32_t)dE, n.scale);
         }
         if (accept) {
           apply_generator(code, f, C);
