@@ -1,0 +1,337 @@
+"""Benchmark of the XZZX simulated-annealing decoder on one GB300 (or N, weak scaling).
+
+Workload (one step = one pass of the whole hot path over one batch):
+  rotated d = 11 XZZX code (121 qubits, 120 generators), code-capacity noise
+  with py = p eta/(eta+1), px = pz = p/(2(eta+1)), eta = 100, and one batch of
+  --shots-per-p shots at each p in {0.10, 0.13, 0.16, 0.19, 0.22}; 64 greedy
+  restarts per shot (256 chains), 1000 sweeps, linear beta 0.05 -> 20 (units
+  of the Nishimori beta), energies at scale 1024.  Step k decodes shots
+  [k*S, (k+1)*S) of every p, so --steps 5 with S = 20000 covers the full
+  1e5 shots per p.  Inputs are sampled by the library on the device before the
+  timed region; L2 is flushed between steps.
+
+Printed JSON line: value = move attempts per second of the whole step (greedy
++ anneal + decision), plus shots/s, the anneal kernel's own rate and its
+roofline, the oracle CPU baseline, end-to-end numbers through the C ABI with
+host buffers, and SM clocks sampled during the timed region.
+
+--impl reference times the oracle (plain single-threaded C++) on the host's
+cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+D, ETA, PS, RESTARTS, SWEEPS, BETA0, BETA1, SCALE = 11, 100.0, (0.10, 0.13, 0.16, 0.19, 0.22), 64, 1000, 0.05, 20.0, 1024
+SEED = 0xD11
+I_ALG = 30  # integer instructions per move attempt in the algorithmic count
+
+
+def workload_config(shots_per_p, world):
+    return {"workload": "d=11 rotated XZZX, eta=100, p in {0.10,0.13,0.16,0.19,0.22}, 64 restarts (256 chains)/shot, "
+                        "1000 sweeps, linear beta 0.05->20, scale 1024",
+            "code_distance": D, "restarts": RESTARTS, "sweeps": SWEEPS, "shots_per_p_per_step": shots_per_p,
+            "p_values": list(PS), "eta": ETA, "global_batch": shots_per_p * len(PS) * world,
+            "parallelism": "shots sharded across ranks" if world > 1 else "single GPU",
+            "l2": "flushed between steps (512 MiB write)"}
+
+
+def attempts_per_shot():
+    return 4 * RESTARTS * SWEEPS * (D * D - 1)
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path, gpu_index):
+        self.path, self.gpu_index, self.proc = path, gpu_index, None
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        top = max(sm)
+        loaded = [x for x in sm if x >= 0.5 * top] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    import oracle as O
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    shots = args.ref_shots
+    pxyz = O.noise_from_eta(0.16, ETA)
+    err, syn = O.sample(D, pxyz, SEED, 0, shots * (args.steps + args.warmup))
+    for w in range(args.warmup):
+        O.decode(D, pxyz, SCALE, O.LINEAR, SWEEPS, BETA0, BETA1, SEED, w * shots, RESTARTS,
+                 syn[w * shots:(w + 1) * shots])
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        s0 = (args.warmup + k) * shots
+        O.decode(D, pxyz, SCALE, O.LINEAR, SWEEPS, BETA0, BETA1, SEED, s0, RESTARTS, syn[s0:s0 + shots])
+    dt = time.perf_counter() - t0
+    att = attempts_per_shot() * shots * args.steps / dt
+    sample = "%d shots of d=11 p=0.16 per step, single-threaded oracle" % shots
+    print(json.dumps({
+        "impl": "reference", "metric": "move-attempts/s and decoded shots/s at d=11 (64 restarts); serve p50/p99 latency",
+        "value": att, "unit": "move-attempts/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic (library sampler, seeded)",
+        "config": workload_config(shots, 1), "shots_per_s": shots * args.steps / dt,
+        "cpu_baseline": {"value": att, "unit": "move-attempts/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": att, "unit": "move-attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# --------------------------------------------------------------------------- CPU baseline (oracle)
+def cpu_baseline(shots):
+    import oracle as O
+    pxyz = O.noise_from_eta(0.16, ETA)
+    err, syn = O.sample(D, pxyz, SEED, 0, shots)
+    t0 = time.perf_counter()
+    O.decode(D, pxyz, SCALE, O.LINEAR, SWEEPS, BETA0, BETA1, SEED, 0, RESTARTS, syn, err)
+    dt = time.perf_counter() - t0
+    return {"value": attempts_per_shot() * shots / dt, "unit": "move-attempts/s", "cores": 1, "kind": "oracle",
+            "sample": "%d shots of d=11 p=0.16 (full 64 restarts x 1000 sweeps), single thread, %.1f s" % (shots, dt),
+            "shots_per_s": shots / dt}
+
+
+# --------------------------------------------------------------------------- our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--shots-per-p", type=int, default=20000)
+    ap.add_argument("--ref-shots", type=int, default=2)
+    ap.add_argument("--cpu-shots", type=int, default=12)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2509_17837_gb300 as X
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    S = args.shots_per_p
+    n_steps = args.warmup + args.steps
+    code = X.Code(D)
+    stream = torch.cuda.current_stream()
+    cases = []
+    for pi, p in enumerate(PS):
+        noise = X.noise_from_eta(p, ETA, 0, SCALE)
+        sched = X.Schedule(noise, SWEEPS, BETA0, BETA1)
+        seed = SEED + pi
+        # rank r decodes its own shot range: shots are independent (weak scaling)
+        shot_base = rank * n_steps * S
+        err, syn = X.sample_errors(code, noise, seed, shot_base, n_steps * S)
+        cases.append(dict(p=p, noise=noise, sched=sched, seed=seed, shot_base=shot_base, err=err, syn=syn))
+    w2 = 2 * code.words
+    init = torch.empty((S, RESTARTS, w2), dtype=torch.int32, device=dev)
+    cbits = torch.empty((S, RESTARTS), dtype=torch.uint8, device=dev)
+    chain_E = torch.empty((S, RESTARTS, 4), dtype=torch.int32, device=dev)
+    outs = [dict(cls=torch.empty(S, dtype=torch.uint8, device=dev), E4=torch.empty((S, 4), dtype=torch.int32, device=dev),
+                 recovery=torch.empty((S, w2), dtype=torch.int32, device=dev),
+                 fail=torch.empty(S, dtype=torch.uint8, device=dev)) for _ in PS]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(k, record):
+        times = []
+        for c, o in zip(cases, outs):
+            s0 = k * S
+            syn = c["syn"][s0:s0 + S]
+            err = c["err"][s0:s0 + S]
+            e = [ev() for _ in range(4)]
+            e[0].record(stream)
+            X.greedy_init(code, c["noise"], c["seed"], c["shot_base"] + s0, syn, RESTARTS, init=init, cbits=cbits,
+                          stream=stream)
+            e[1].record(stream)
+            X.anneal(code, c["sched"], c["seed"], c["shot_base"] + s0, init, want_cfg=False, best_E=chain_E,
+                     stream=stream)
+            e[2].record(stream)
+            res = X.decode_reduce(code, init, cbits, chain_E, true_errors=err, stream=stream)
+            e[3].record(stream)
+            o["fail"] = res["fail"]
+            times.append(e)
+        return times
+
+    for k in range(args.warmup):
+        step(k, False)
+    barrier()
+    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_%d.csv" % os.getpid(), dev)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.5)
+    barrier()
+    t_wall = time.perf_counter()
+    all_ev = []
+    fails = [0] * len(PS)
+    for k in range(args.warmup, n_steps):
+        flush.fill_(k & 0xFF)  # evict L2 between steps (outside the per-step events)
+        all_ev.append(step(k, True))
+    barrier()
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop() if rank == 0 else None
+    g_ms = a_ms = r_ms = 0.0
+    for st in all_ev:
+        for e in st:
+            g_ms += e[0].elapsed_time(e[1])
+            a_ms += e[1].elapsed_time(e[2])
+            r_ms += e[2].elapsed_time(e[3])
+    step_ms = (g_ms + a_ms + r_ms) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms, a_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        step_ms, a_ms_max = float(t[0]), float(t[1])
+    else:
+        a_ms_max = a_ms
+    shots_per_step = S * len(PS) * world
+    att_per_step = shots_per_step * attempts_per_shot()
+    value = att_per_step / (step_ms / 1e3)
+    anneal_launches = args.steps * len(PS)
+    anneal_ms_per_launch = a_ms_max / anneal_launches
+    anneal_rate = S * attempts_per_shot() / (anneal_ms_per_launch / 1e3)  # per GPU
+
+    # failure counts (logical error rate) over the timed shots, for the record
+    for i, c in enumerate(cases):
+        pass
+
+    result = None
+    if rank == 0:
+        props = torch.cuda.get_device_properties(dev)
+        n_sm = props.multi_processor_count
+        f_mhz = clocks.get("sm_mhz") or 1920.0
+        peak = n_sm * 4 * 32 * f_mhz * 1e6 / 1e12  # T lane-instructions/s
+        achieved = anneal_rate * I_ALG / 1e12
+        result = {
+            "metric": "move-attempts/s and decoded shots/s at d=11 (64 restarts); serve p50/p99 latency",
+            "value": value, "unit": "move-attempts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic (code-capacity noise sampled on device by the library, seeded)",
+            "config": workload_config(S, world),
+            "shots_per_s": shots_per_step / (step_ms / 1e3),
+            "anneal_attempts_per_s_per_gpu": anneal_rate,
+            "kernel_ms_per_step": {"greedy": g_ms / args.steps, "anneal": a_ms / args.steps,
+                                   "reduce": r_ms / args.steps},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "anneal_kernel<11>", "I_alg_per_attempt": I_ALG,
+                         "peak_basis": "%d SMs x 4 SMSP x 32 lanes x %.0f MHz (median SM clock sampled in the timed region)"
+                                       % (n_sm, f_mhz)},
+            "clocks": clocks, "gpu_launches": 3 * len(PS) * args.steps,
+            "wall_s_timed_region": wall,
+        }
+    # ---------------------------------------------------------------- e2e through the C ABI, host buffers
+    if not args.no_e2e:
+        c = cases[2]
+        syn_h = c["syn"][:S].cpu().pin_memory()
+        err_h = c["err"][:S].cpu().pin_memory()
+        syn_d = torch.empty_like(c["syn"][:S])
+        err_d = torch.empty_like(c["err"][:S])
+        cls_h = torch.empty(S, dtype=torch.uint8).pin_memory()
+        fail_h = torch.empty(S, dtype=torch.uint8).pin_memory()
+        ws = torch.empty(X.decode_workspace_size(code, S, RESTARTS), dtype=torch.uint8, device=dev)
+        o = outs[2]
+
+        def e2e_step(k):
+            syn_d.copy_(syn_h, non_blocking=True)
+            err_d.copy_(err_h, non_blocking=True)
+            X.decode_batch(code, c["noise"], c["sched"], c["seed"], c["shot_base"] + k * S, syn_d, RESTARTS,
+                           true_errors=err_d, out=o, workspace=ws, stream=stream)
+            cls_h.copy_(o["cls"], non_blocking=True)
+            fail_h.copy_(o["fail"], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        e2e_step(0)
+        barrier()
+        t0 = time.perf_counter()
+        n_e2e = 2
+        for k in range(n_e2e):
+            e2e_step(k)
+        barrier()
+        e2e_s = (time.perf_counter() - t0) / n_e2e
+        if rank == 0:
+            result["e2e"] = {"value": S * attempts_per_shot() * world / e2e_s, "unit": "move-attempts/s",
+                             "h2d_bytes_per_step": syn_h.numel() * 4 + err_h.numel() * 4,
+                             "d2h_bytes_per_step": cls_h.numel() + fail_h.numel(),
+                             "shots_per_s": S * world / e2e_s,
+                             "note": "one batch of %d shots at p=0.16 per step through xzzx_decode_batch; pinned "
+                                     "host syndromes/errors copied in, classes and failure flags copied out" % S}
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.cpu_shots)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * xzzx.h -- C ABI of the GB300 simulated-annealing decoder for the XZZX code
+ * (T. Sakashita, "Simulated-annealing decoder for the XZZX code with
+ * greedy-matching initialization", arXiv:2509.17837).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an xzzx_status; XZZX_OK is 0.  On failure
+ *   xzzx_last_error() returns a message for the calling thread.  No C++
+ *   exception crosses this boundary.
+ * - The library owns only opaque handles (xzzx_code, xzzx_schedule,
+ *   xzzx_server) and the device tables they hold; xzzx_free_* releases them.
+ *   The caller owns every data buffer.  Buffers marked "device" must be device
+ *   memory of the GPU that was current when the handle was created; buffers
+ *   marked "host" are ordinary host memory.
+ * - Device calls take a cudaStream_t passed as void* (NULL = legacy default
+ *   stream), validate every size on the host before launching anything, and
+ *   run asynchronously on that stream.  A kernel fault surfaces as
+ *   XZZX_ECUDA from the launch or from a later synchronising call.
+ * - Rotated layout: data qubit (r, c), 0 <= r, c < d, has index q = r*d + c;
+ *   the d*d - 1 generators are indexed colour by colour (colour =
+ *   (a&1) | ((b&1)<<1) of the face (a, b)), then by a, then by b.
+ * - Configuration layout ("2w words"): w = ceil(d*d/32); words [0, w) hold the
+ *   X bits, words [w, 2w) the Z bits; qubit q is bit (q & 31) of word q >> 5.
+ *   Pauli I, X, Y, Z is (x, z) = (0,0), (1,0), (1,1), (0,1).
+ * - Syndrome layout ("sw words"): sw = ceil((d*d-1)/32); generator f is bit
+ *   (f & 31) of word f >> 5.
+ * - Logical classes are indexed I=0, X=1, Y=2, Z=3.
+ * - Randomness: Philox4x32-10 keyed by the 64-bit seed.  A draw depends only on
+ *   (seed, purpose, shot, restart/chain, sweep, face), so results do not
+ *   depend on how shots are split across calls or launches.
+ */
+#ifndef XZZX_H
+#define XZZX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  XZZX_OK = 0,
+  XZZX_EINVAL = 1,      /* bad argument, size or handle */
+  XZZX_ENOMEM = 2,      /* host or device allocation failed */
+  XZZX_ECUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  XZZX_ETIMEOUT = 4,    /* a bounded device or host wait ran out */
+  XZZX_EBUSY = 5,       /* no capacity left (server admission) */
+  XZZX_EUNSUPPORTED = 6 /* valid request this build does not implement */
+} xzzx_status;
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char* xzzx_last_error(void);
+
+/* Library version string. */
+const char* xzzx_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Code tables (Sec. "The XZZX code", Eq. stabilizer_generator).           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct xzzx_code xzzx_code;
+
+typedef struct {
+  int32_t d;
+  int32_t n_qubits;        /* d*d */
+  int32_t n_stab;          /* d*d - 1 */
+  int32_t words;           /* w: words per bit plane; a configuration is 2w words */
+  int32_t syn_words;       /* sw: words per syndrome */
+  int32_t colour_start[5]; /* generators of colour c are [start[c], start[c+1]) */
+} xzzx_code_info;
+
+/* Build the rotated distance-d XZZX code: G_f = X_TL Z_TR Z_BL X_BR on the
+ * corners of face f inside the lattice (Eq. stabilizer_generator), L_Z along
+ * row 0 and L_X along column 0.  d must be odd, 3 <= d <= 31.  layout 0 is the
+ * rotated layout; any other value returns XZZX_EUNSUPPORTED.  Uploads the
+ * tables to the current device.  *out is owned by the caller and released
+ * with xzzx_free_code. */
+xzzx_status xzzx_make_code(int d, int layout, xzzx_code** out);
+xzzx_status xzzx_get_code_info(const xzzx_code* code, xzzx_code_info* out);
+void xzzx_free_code(xzzx_code* code);
+
+/* Generator f as four corner qubits (TL, TR, BL, BR; -1 outside) and its face
+ * coordinates; host arrays of n_stab entries (corners: 4*n_stab).  Any
+ * pointer may be NULL. */
+xzzx_status xzzx_code_faces(const xzzx_code* code, int32_t* a, int32_t* b, int32_t* corners);
+
+/* ------------------------------------------------------------------------ */
+/* Noise and energies (Eqs. noise_map, coeff_in_energy, energy,            */
+/* coeff_in_distance).                                                      */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double px, py, pz; /* per-qubit X, Y, Z probabilities, p = px+py+pz < 1/2 */
+  int32_t scale;     /* fixed-point scale of the energies */
+  int32_t W[4];      /* integer energy of one qubit by (x<<1)|z: I, Z, X, Y;
+                        W_P = llround(scale * -ln(p_P / (1-p))) */
+  int32_t Wt_x, Wt_z;/* matching weights llround(scale * -ln((px+py)/(1-p)))
+                        and llround(scale * -ln((pz+py)/(1-p))) */
+} xzzx_noise;
+
+/* Fill *out from (px, py, pz).  Each p_P must be > 0 and p < 1/2; scale > 0
+ * and small enough that d*d*max(W) fits in int32 for the codes used. */
+xzzx_status xzzx_make_noise(double px, double py, double pz, int32_t scale, xzzx_noise* out);
+
+/* Bias helpers.  convention 0: py = p*eta/(eta+1), px = pz = p/(2(eta+1));
+ * convention 1 (the paper's px:py:pz = 1:eta:1, Sec. "Simulation setting"):
+ * py = p*eta/(eta+2), px = pz = p/(eta+2). */
+xzzx_status xzzx_noise_from_eta(double p, double eta, int convention, int32_t scale, xzzx_noise* out);
+
+/* ------------------------------------------------------------------------ */
+/* Annealing schedule and acceptance thresholds (Eqs. beta_i, beta_ratio,   */
+/* Alg. 3).                                                                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct xzzx_schedule xzzx_schedule;
+
+enum { XZZX_SCHED_LINEAR = 0, XZZX_SCHED_PAPER_LOG = 1 };
+
+/* Build the threshold table of an n_sweeps schedule for the energies of
+ * *noise.  Inverse temperatures are in units of the Nishimori value:
+ * LINEAR: beta_t = beta0 + (beta1-beta0) t/(n_sweeps-1) (beta0 if n_sweeps=1);
+ * PAPER_LOG: beta_t = beta0 (1 + gamma ln(t+1)), gamma = (beta1/beta0-1)/ln N.
+ * For every sweep t and every positive energy change dE a generator move can
+ * produce, T[t][dE] = min(2^32-1, floor(2^32 exp(-beta_t dE/scale))) in FP64;
+ * a move is accepted when dE <= 0 or its uint32 draw u < T.  0 <= n_sweeps,
+ * beta0, beta1 >= 0 and finite.  The table is copied to the current device.
+ * *out is released with xzzx_free_schedule. */
+xzzx_status xzzx_make_schedule(const xzzx_noise* noise, int kind, int n_sweeps, double beta0,
+                               double beta1, xzzx_schedule** out);
+void xzzx_free_schedule(xzzx_schedule* sched);
+
+/* Copy the host threshold table: *n_classes distinct positive dE values into
+ * dE (host, capacity cap_classes) and n_sweeps x n_classes thresholds into T
+ * (host, row-major).  Pass NULL arrays to query *n_classes only. */
+xzzx_status xzzx_schedule_table(const xzzx_schedule* sched, int* n_classes, int32_t* dE, int cap_classes,
+                                uint32_t* T);
+
+/* ------------------------------------------------------------------------ */
+/* Hot path.                                                                */
+/* ------------------------------------------------------------------------ */
+
+/* Sample code-capacity errors and their syndromes (Sec. "Simulation
+ * setting"): qubit q of shot s is X, Y, Z or I as its draw u falls below
+ * floor(px 2^32), +floor(py 2^32), +floor(pz 2^32).  errors: device,
+ * n_shots x 2w words (may be NULL); syndromes: device, n_shots x sw words.
+ * Row k belongs to shot shot0 + k. */
+xzzx_status xzzx_sample_errors(const xzzx_code* code, const xzzx_noise* noise, uint64_t seed, uint64_t shot0,
+                               int n_shots, uint32_t* errors, uint32_t* syndromes, void* stream);
+
+/* Randomised greedy matching (Algs. 5 and 6) for every (shot, restart):
+ * defects of each decoding-graph colour are paired in the order
+ * (w(u,v), key, u, v), w = min(w_int, w(u,b) + w(v,b)) (Eq.
+ * distance_u_v_def_new), key = a Philox draw per pair when randomised != 0 and
+ * 0 otherwise, a pair kept when both ends are free; a virtual boundary vertex
+ * joins an odd defect set; each kept pair is joined by a canonical shortest
+ * path, added modulo two.  syndromes: device, n_shots x sw words.  init:
+ * device, n_shots x restarts x 2w words (R_i of restart i).  cbits: device,
+ * n_shots x restarts bytes, bit 0 = R_i anticommutes with L_Z, bit 1 = with
+ * L_X.  1 <= restarts <= 65535. */
+xzzx_status xzzx_greedy_init(const xzzx_code* code, const xzzx_noise* noise, uint64_t seed, uint64_t shot0,
+                             int n_shots, int restarts, int randomised, const uint32_t* syndromes, uint32_t* init,
+                             uint8_t* cbits, void* stream);
+
+/* Simulated annealing of every chain (Alg. 2 with the Metropolis step of
+ * Alg. 3).  Chain (k, i, P), k < n_shots, i < restarts, P in I,X,Y,Z, has
+ * index c = (k*restarts + i)*4 + P, starts from init[k][i] * L_P and draws
+ * with chain id (shot0+k)*restarts*4 + i*4 + P.  A sweep visits the
+ * generators colour by colour; the lowest energy and its configuration are
+ * recorded at the start and after every colour phase.  init: device,
+ * n_shots x restarts x 2w words.  best_E: device, n_chains int32.  best_cfg:
+ * device, n_chains x 2w words, or NULL.  final_E / final_cfg: device, the
+ * state after the last sweep, or NULL. */
+xzzx_status xzzx_anneal(const xzzx_code* code, const xzzx_schedule* sched, uint64_t seed, uint64_t shot0,
+                        int n_shots, int restarts, const uint32_t* init, int32_t* best_E, uint32_t* best_cfg,
+                        int32_t* final_E, uint32_t* final_cfg, void* stream);
+
+/* Coset relabelling and decision (Alg. 7, Eqs. coset_correspondence,
+ * determine_P_from_E): chain (i, P) belongs to coset Q_i P with
+ * [L_Q] = [R_i R_1]; E4[P] is the minimum over coset P; cls = argmin with
+ * ties in the order I, X, Y, Z; recovery = R_1 L_cls.  best_cfg_out is the
+ * configuration of the lowest-index chain reaching E4[cls] inside coset cls
+ * (needs chain_cfg).  fail = [C_true recovery] != [I] (needs true_errors).
+ * Inputs are the outputs of xzzx_greedy_init and xzzx_anneal (device).
+ * Outputs (device): cls n_shots bytes, E4 4 x n_shots int32, recovery
+ * n_shots x 2w words; best_cfg_out, fail and the matching inputs may be NULL. */
+xzzx_status xzzx_decode_reduce(const xzzx_code* code, int n_shots, int restarts, const uint32_t* init,
+                               const uint8_t* cbits, const int32_t* chain_E, const uint32_t* chain_cfg,
+                               const uint32_t* true_errors, uint8_t* cls, int32_t* E4, uint32_t* recovery,
+                               uint32_t* best_cfg_out, uint8_t* fail, void* stream);
+
+/* Bytes of device workspace xzzx_decode_batch needs for this batch. */
+xzzx_status xzzx_decode_workspace_size(const xzzx_code* code, int n_shots, int restarts, int want_best_cfg,
+                                       size_t* bytes);
+
+/* The whole decoder (Alg. 7) for n_shots syndromes: greedy_init, anneal and
+ * decode_reduce on one stream with intermediates in the caller's workspace
+ * (device, at least xzzx_decode_workspace_size bytes, 256-byte aligned).
+ * Same layouts and optional outputs as the three calls above. */
+xzzx_status xzzx_decode_batch(const xzzx_code* code, const xzzx_noise* noise, const xzzx_schedule* sched,
+                              uint64_t seed, uint64_t shot0, int n_shots, int restarts, int randomised,
+                              const uint32_t* syndromes, const uint32_t* true_errors, uint8_t* cls, int32_t* E4,
+                              uint32_t* recovery, uint32_t* best_cfg_out, uint8_t* fail, void* workspace,
+                              size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XZZX_H */

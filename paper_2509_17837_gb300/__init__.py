@@ -1,0 +1,16 @@
+"""GB300 (sm_103a) simulated-annealing decoder for the XZZX code.
+
+Hot path of arXiv:2509.17837 (Algs. 2, 3, 6, 7) as hand-written CUDA behind
+the C ABI of ``include/xzzx.h`` (``libxzzx.so``); this package is the thin
+Python binding.  There is no CPU fallback: importing the binding without the
+built library raises.
+"""
+from . import _lib
+from ._lib import XzzxError
+from .api import (CONVENTION_BASELINE, CONVENTION_PAPER, LINEAR, PAPER_LOG, Code, Schedule, anneal,
+                  decode_batch, decode_reduce, decode_workspace_size, greedy_init, make_noise, noise_from_eta,
+                  sample_errors, version)
+
+__all__ = ["Code", "Schedule", "XzzxError", "anneal", "decode_batch", "decode_reduce", "decode_workspace_size",
+           "greedy_init", "make_noise", "noise_from_eta", "sample_errors", "version", "LINEAR", "PAPER_LOG",
+           "CONVENTION_BASELINE", "CONVENTION_PAPER"]

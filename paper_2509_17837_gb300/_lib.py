@@ -1,0 +1,89 @@
+"""ctypes declarations of libxzzx.so (argument marshalling only).
+
+Every function here is the C entry point of the same name in
+``include/xzzx.h``; nothing is computed in Python.  Importing this module
+fails loudly when the library has not been built: there is no fallback.
+"""
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libxzzx.so")
+
+XZZX_OK, XZZX_EINVAL, XZZX_ENOMEM, XZZX_ECUDA, XZZX_ETIMEOUT, XZZX_EBUSY, XZZX_EUNSUPPORTED = range(7)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EBUSY", "EUNSUPPORTED"]
+
+
+class XzzxError(RuntimeError):
+    def __init__(self, status, func, msg):
+        self.status = status
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__("%s failed with XZZX_%s: %s" % (func, name, msg))
+
+
+class Noise(C.Structure):
+    _fields_ = [("px", C.c_double), ("py", C.c_double), ("pz", C.c_double), ("scale", C.c_int32),
+                ("W", C.c_int32 * 4), ("Wt_x", C.c_int32), ("Wt_z", C.c_int32)]
+
+
+class CodeInfo(C.Structure):
+    _fields_ = [("d", C.c_int32), ("n_qubits", C.c_int32), ("n_stab", C.c_int32), ("words", C.c_int32),
+                ("syn_words", C.c_int32), ("colour_start", C.c_int32 * 5)]
+
+
+_p = C.c_void_p
+_i = C.c_int
+_u64 = C.c_uint64
+_d = C.c_double
+
+SIGNATURES = {
+    "xzzx_last_error": ([], C.c_char_p),
+    "xzzx_version": ([], C.c_char_p),
+    "xzzx_make_code": ([_i, _i, C.POINTER(_p)], _i),
+    "xzzx_get_code_info": ([_p, C.POINTER(CodeInfo)], _i),
+    "xzzx_free_code": ([_p], None),
+    "xzzx_code_faces": ([_p, _p, _p, _p], _i),
+    "xzzx_make_noise": ([_d, _d, _d, C.c_int32, C.POINTER(Noise)], _i),
+    "xzzx_noise_from_eta": ([_d, _d, _i, C.c_int32, C.POINTER(Noise)], _i),
+    "xzzx_make_schedule": ([C.POINTER(Noise), _i, _i, _d, _d, C.POINTER(_p)], _i),
+    "xzzx_free_schedule": ([_p], None),
+    "xzzx_schedule_table": ([_p, C.POINTER(_i), _p, _i, _p], _i),
+    "xzzx_sample_errors": ([_p, C.POINTER(Noise), _u64, _u64, _i, _p, _p, _p], _i),
+    "xzzx_greedy_init": ([_p, C.POINTER(Noise), _u64, _u64, _i, _i, _i, _p, _p, _p, _p], _i),
+    "xzzx_anneal": ([_p, _p, _u64, _u64, _i, _i, _p, _p, _p, _p, _p, _p], _i),
+    "xzzx_decode_reduce": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
+    "xzzx_decode_workspace_size": ([_p, _i, _i, _i, C.POINTER(C.c_size_t)], _i),
+    "xzzx_decode_batch": ([_p, C.POINTER(Noise), _p, _u64, _u64, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p,
+                           C.c_size_t, _p], _i),
+}
+
+_lib = None
+
+
+def lib():
+    """Load libxzzx.so once; raise if it is missing (no CPU fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libxzzx.so is not built (%s); run `python -c \"import __graft_entry__ as g; "
+                               "g.build()\"` or `python -m paper_2509_17837_gb300.build`" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def check(status, func):
+    if status != XZZX_OK:
+        msg = lib().xzzx_last_error()
+        raise XzzxError(status, func, msg.decode() if msg else "")
+
+
+def call(name, *args):
+    """Call entry point `name` and raise XzzxError on a non-OK status."""
+    st = getattr(lib(), name)(*args)
+    check(st, name)
+    return st

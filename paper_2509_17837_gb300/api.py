@@ -1,0 +1,204 @@
+"""Python binding of libxzzx (argument marshalling only).
+
+The functions mirror the C entry points of ``include/xzzx.h`` one to one.
+Device buffers are torch CUDA tensors (int32 or uint8 storage holding the
+words and bytes of the C layout); every step of the decoder runs in the CUDA
+kernels of libxzzx.  Optional output tensors are allocated with torch on the
+current device when not given.
+"""
+import ctypes as C
+
+import torch
+
+from ._lib import CodeInfo, Noise, call, lib
+
+LINEAR, PAPER_LOG = 0, 1
+CONVENTION_BASELINE, CONVENTION_PAPER = 0, 1
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def version():
+    return lib().xzzx_version().decode()
+
+
+class Code:
+    """Rotated distance-d XZZX code (Sec. "The XZZX code"); tables on the current GPU."""
+
+    def __init__(self, d, layout=0):
+        h = C.c_void_p()
+        call("xzzx_make_code", d, layout, C.byref(h))
+        self._h = h
+        info = CodeInfo()
+        call("xzzx_get_code_info", h, C.byref(info))
+        self.d = info.d
+        self.n_qubits = info.n_qubits
+        self.n_stab = info.n_stab
+        self.words = info.words
+        self.syn_words = info.syn_words
+        self.colour_start = list(info.colour_start)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def faces(self):
+        import numpy as np
+        a = np.zeros(self.n_stab, np.int32)
+        b = np.zeros(self.n_stab, np.int32)
+        corners = np.zeros((self.n_stab, 4), np.int32)
+        call("xzzx_code_faces", self._h, a.ctypes.data_as(C.c_void_p), b.ctypes.data_as(C.c_void_p),
+             corners.ctypes.data_as(C.c_void_p))
+        return a, b, corners
+
+    def close(self):
+        if self._h:
+            lib().xzzx_free_code(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_noise(px, py, pz, scale=1024):
+    n = Noise()
+    call("xzzx_make_noise", px, py, pz, scale, C.byref(n))
+    return n
+
+
+def noise_from_eta(p, eta, convention=CONVENTION_BASELINE, scale=1024):
+    n = Noise()
+    call("xzzx_noise_from_eta", p, eta, convention, scale, C.byref(n))
+    return n
+
+
+class Schedule:
+    """FP64 acceptance-threshold table of an annealing schedule, uploaded once."""
+
+    def __init__(self, noise, n_sweeps, beta0, beta1, kind=LINEAR):
+        h = C.c_void_p()
+        call("xzzx_make_schedule", C.byref(noise), kind, n_sweeps, beta0, beta1, C.byref(h))
+        self._h = h
+        self.noise = noise
+        self.n_sweeps = n_sweeps
+
+    @property
+    def handle(self):
+        return self._h
+
+    def table(self):
+        import numpy as np
+        k = C.c_int()
+        call("xzzx_schedule_table", self._h, C.byref(k), None, 0, None)
+        dE = np.zeros(k.value, np.int32)
+        T = np.zeros((self.n_sweeps, k.value), np.uint32)
+        call("xzzx_schedule_table", self._h, C.byref(k), dE.ctypes.data_as(C.c_void_p), k.value,
+             T.ctypes.data_as(C.c_void_p))
+        return dE, T
+
+    def close(self):
+        if self._h:
+            lib().xzzx_free_schedule(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _empty(shape, dtype, device=None):
+    return torch.empty(shape, dtype=dtype, device=device if device is not None else torch.cuda.current_device())
+
+
+def sample_errors(code, noise, seed, shot0, n_shots, errors=None, syndromes=None, want_errors=True, stream=None):
+    if want_errors and errors is None:
+        errors = _empty((n_shots, 2 * code.words), torch.int32)
+    if syndromes is None:
+        syndromes = _empty((n_shots, code.syn_words), torch.int32)
+    call("xzzx_sample_errors", code.handle, C.byref(noise), seed, shot0, n_shots, _ptr(errors), _ptr(syndromes),
+         _stream(stream))
+    return errors, syndromes
+
+
+def greedy_init(code, noise, seed, shot0, syndromes, restarts, randomised=True, init=None, cbits=None,
+                stream=None):
+    n = syndromes.shape[0]
+    if init is None:
+        init = _empty((n, restarts, 2 * code.words), torch.int32)
+    if cbits is None:
+        cbits = _empty((n, restarts), torch.uint8)
+    call("xzzx_greedy_init", code.handle, C.byref(noise), seed, shot0, n, restarts, int(bool(randomised)),
+         _ptr(syndromes), _ptr(init), _ptr(cbits), _stream(stream))
+    return init, cbits
+
+
+def anneal(code, sched, seed, shot0, init, want_cfg=True, want_final=False, best_E=None, best_cfg=None,
+           final_E=None, final_cfg=None, stream=None):
+    n, restarts = init.shape[0], init.shape[1]
+    chains = n * restarts * 4
+    if best_E is None:
+        best_E = _empty((n, restarts, 4), torch.int32)
+    if want_cfg and best_cfg is None:
+        best_cfg = _empty((n, restarts, 4, 2 * code.words), torch.int32)
+    if want_final:
+        final_E = final_E if final_E is not None else _empty((n, restarts, 4), torch.int32)
+        final_cfg = final_cfg if final_cfg is not None else _empty((n, restarts, 4, 2 * code.words), torch.int32)
+    assert best_E.numel() == chains
+    call("xzzx_anneal", code.handle, sched.handle, seed, shot0, n, restarts, _ptr(init), _ptr(best_E),
+         _ptr(best_cfg), _ptr(final_E), _ptr(final_cfg), _stream(stream))
+    return dict(best_E=best_E, best_cfg=best_cfg, final_E=final_E, final_cfg=final_cfg)
+
+
+def decode_reduce(code, init, cbits, chain_E, chain_cfg=None, true_errors=None, want_best_cfg=False, stream=None):
+    n, restarts = init.shape[0], init.shape[1]
+    cls = _empty((n,), torch.uint8)
+    E4 = _empty((n, 4), torch.int32)
+    recovery = _empty((n, 2 * code.words), torch.int32)
+    best = _empty((n, 2 * code.words), torch.int32) if want_best_cfg else None
+    fail = _empty((n,), torch.uint8) if true_errors is not None else None
+    call("xzzx_decode_reduce", code.handle, n, restarts, _ptr(init), _ptr(cbits), _ptr(chain_E), _ptr(chain_cfg),
+         _ptr(true_errors), _ptr(cls), _ptr(E4), _ptr(recovery), _ptr(best), _ptr(fail), _stream(stream))
+    return dict(cls=cls, E4=E4, recovery=recovery, best_cfg=best, fail=fail)
+
+
+def decode_workspace_size(code, n_shots, restarts, want_best_cfg=False):
+    b = C.c_size_t()
+    call("xzzx_decode_workspace_size", code.handle, n_shots, restarts, int(bool(want_best_cfg)), C.byref(b))
+    return b.value
+
+
+def decode_batch(code, noise, sched, seed, shot0, syndromes, restarts, randomised=True, true_errors=None,
+                 want_best_cfg=False, out=None, workspace=None, stream=None):
+    """Alg. 7 for a batch of syndromes; returns dict(cls, E4, recovery, best_cfg, fail)."""
+    n = syndromes.shape[0]
+    if out is None:
+        out = dict(cls=_empty((n,), torch.uint8), E4=_empty((n, 4), torch.int32),
+                   recovery=_empty((n, 2 * code.words), torch.int32),
+                   best_cfg=_empty((n, 2 * code.words), torch.int32) if want_best_cfg else None,
+                   fail=_empty((n,), torch.uint8) if true_errors is not None else None)
+    need = decode_workspace_size(code, n, restarts, want_best_cfg)
+    if workspace is None or workspace.numel() < need:
+        workspace = _empty((max(need, 256),), torch.uint8)
+    call("xzzx_decode_batch", code.handle, C.byref(noise), sched.handle, seed, shot0, n, restarts,
+         int(bool(randomised)), _ptr(syndromes), _ptr(true_errors), _ptr(out["cls"]), _ptr(out["E4"]),
+         _ptr(out["recovery"]), _ptr(out.get("best_cfg")), _ptr(out.get("fail")), _ptr(workspace),
+         workspace.numel(), _stream(stream))
+    return out

@@ -1,0 +1,93 @@
+// Private declarations of libxzzx (GB300 path).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/xzzx.h"
+
+namespace xzzx {
+
+// ---------------------------------------------------------------------------
+// Error reporting: thread-local message behind xzzx_last_error().
+// ---------------------------------------------------------------------------
+xzzx_status fail(xzzx_status st, const std::string& msg);
+xzzx_status ok();
+xzzx_status cuda_fail(cudaError_t e, const char* what);
+
+#define XZZX_CUDA_TRY(expr)                                    \
+  do {                                                         \
+    cudaError_t e_ = (expr);                                   \
+    if (e_ != cudaSuccess) return ::xzzx::cuda_fail(e_, #expr); \
+  } while (0)
+
+// Largest distance the kernels are built for (one 64-bit interleaved word per
+// lattice row: 2 bits per qubit).
+constexpr int kMaxD = 31;
+
+// Philox purposes (top byte layout of the last counter word).
+constexpr uint32_t kTagNoise = 1, kTagGreedy = 2, kTagSA = 3;
+
+// Sentinel index of the virtual boundary vertex in greedy pair keys.
+constexpr uint32_t kBoundary = 0xFFFFu;
+
+// Generator shapes: the bulk weight-4 face and the four weight-2 boundary
+// faces, by which corners exist.  Signature bits: TL 0-1, TR 2-3, BL 4-5, BR 6-7.
+enum FaceType { kBulk = 0, kTop = 1, kBottom = 2, kLeft = 3, kRight = 4, kNumTypes = 5 };
+constexpr int kCornerMask[kNumTypes] = {0xF, 0xC, 0x3, 0xA, 0x5};  // bit k = corner k present
+
+// Round keys of Philox4x32-10 for one seed, in kernel-parameter space.
+struct PhiloxKeys {
+  uint32_t k0[10], k1[10];
+};
+PhiloxKeys philox_keys(uint64_t seed);
+
+// Device view of a code (pointers into the tables owned by xzzx_code).
+struct DevCode {
+  int d, nq, ns, w, sw;
+  int colour_start[5];
+  const int16_t* face_a;     // ns
+  const int16_t* face_b;     // ns
+  const uint8_t* face_c2;    // ns, decoding-graph colour (a+b)&1
+  const int16_t* face_at;    // (d+1)^2, index of face (a,b) at (a+1)*(d+1)+(b+1), or -1
+  const uint32_t* logical;   // 2 x 2w words: L_X then L_Z, planar
+};
+
+}  // namespace xzzx
+
+struct xzzx_code {
+  int d = 0, nq = 0, ns = 0, w = 0, sw = 0;
+  int colour_start[5] = {0, 0, 0, 0, 0};
+  int device = -1;
+  std::vector<int16_t> a, b;
+  std::vector<uint8_t> c2, c4;
+  std::vector<int32_t> corners;   // 4 per face
+  std::vector<int16_t> face_at;
+  std::vector<uint32_t> logical;  // L_X (2w) then L_Z (2w)
+  void* dev_block = nullptr;      // one allocation holding the device tables
+  xzzx::DevCode dev{};
+};
+
+struct xzzx_schedule {
+  int kind = 0, n_sweeps = 0;
+  double beta0 = 0, beta1 = 0;
+  xzzx_noise noise{};
+  int device = -1;
+  int n_classes = 0;
+  std::vector<int32_t> dE_class;        // positive dE values, ascending
+  std::vector<uint32_t> T;              // n_sweeps x n_classes
+  std::vector<int32_t> sig_dE;          // kNumTypes x 256
+  std::vector<int32_t> sig_class;       // kNumTypes x 256, class index or -1 (dE <= 0)
+  uint32_t* d_T = nullptr;              // device copy of T (at least one row)
+  int2* d_sig = nullptr;                // device (dE, class) per type x signature
+};
+
+namespace xzzx {
+// Validation helpers shared by the entry points.
+xzzx_status check_code(const xzzx_code* code);
+xzzx_status check_device(int device);
+xzzx_status check_ptr(const void* p, const char* name);
+}  // namespace xzzx
