@@ -204,6 +204,31 @@ xzzx_status xzzx_decode_batch(const xzzx_code* code, const xzzx_noise* noise, co
                               uint32_t* recovery, uint32_t* best_cfg_out, uint8_t* fail, void* workspace,
                               size_t workspace_bytes, void* stream);
 
+/* Size of the scratch array built into the library for
+ * xzzx_decode_batch_static (per GPU, held until the process exits). */
+#define XZZX_STATIC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory while they run, for example a decoder
+ * inside a control loop whose GPU memory is fixed at start-up, or a C host
+ * that only receives device buffers from another component.  It does what
+ * xzzx_decode_batch does, with the same arguments minus the workspace: the
+ * intermediates live in a scratch array compiled into the library, so the
+ * call performs no allocation (no cudaMalloc, no allocating library call).
+ * Returns XZZX_EINVAL when the batch's intermediates
+ * (xzzx_decode_workspace_size) exceed XZZX_STATIC_SCRATCH_BYTES; split such
+ * batches.  All calls share the one array: calls whose work overlaps on the
+ * GPU race on it, so the caller must serialise them.  No scratch byte needs
+ * to start at zero (each call writes what it reads).  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress, once
+ * per device, that device current); make that first call before any stream
+ * capture. */
+xzzx_status xzzx_decode_batch_static(const xzzx_code* code, const xzzx_noise* noise, const xzzx_schedule* sched,
+                                     uint64_t seed, uint64_t shot0, int n_shots, int restarts, int randomised,
+                                     const uint32_t* syndromes, const uint32_t* true_errors, uint8_t* cls,
+                                     int32_t* E4, uint32_t* recovery, uint32_t* best_cfg_out, uint8_t* fail,
+                                     void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -55,6 +55,8 @@ SIGNATURES = {
     "xzzx_decode_workspace_size": ([_p, _i, _i, _i, C.POINTER(C.c_size_t)], _i),
     "xzzx_decode_batch": ([_p, C.POINTER(Noise), _p, _u64, _u64, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p,
                            C.c_size_t, _p], _i),
+    "xzzx_decode_batch_static": ([_p, C.POINTER(Noise), _p, _u64, _u64, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p,
+                                  _p], _i),
 }
 
 _lib = None
