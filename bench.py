@@ -47,6 +47,21 @@ def attempts_per_shot():
     return 4 * RESTARTS * SWEEPS * (D * D - 1)
 
 
+def rank_shot_base(rank, n_steps, shots_per_step):
+    """First shot index of a rank's own range.  Shots are independent and every
+    draw is keyed by the absolute shot index, so ranks decode disjoint ranges
+    with no data exchange (weak scaling)."""
+    return rank * n_steps * shots_per_step
+
+
+def max_over_ranks(values, dist, device):
+    """Element-wise MAX of per-rank timings (the slowest rank sets the time)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -189,7 +204,7 @@ def main():
         sched = X.Schedule(noise, SWEEPS, BETA0, BETA1)
         seed = SEED + pi
         # rank r decodes its own shot range: shots are independent (weak scaling)
-        shot_base = rank * n_steps * S
+        shot_base = rank_shot_base(rank, n_steps, S)
         err, syn = X.sample_errors(code, noise, seed, shot_base, n_steps * S)
         cases.append(dict(p=p, noise=noise, sched=sched, seed=seed, shot_base=shot_base, err=err, syn=syn))
     w2 = 2 * code.words
@@ -248,9 +263,7 @@ def main():
             r_ms += e[2].elapsed_time(e[3])
     step_ms = (g_ms + a_ms + r_ms) / args.steps
     if world > 1:
-        t = torch.tensor([step_ms, a_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms, a_ms_max = float(t[0]), float(t[1])
+        step_ms, a_ms_max = max_over_ranks([step_ms, a_ms], dist, dev)
     else:
         a_ms_max = a_ms
     shots_per_step = S * len(PS) * world
@@ -259,10 +272,6 @@ def main():
     anneal_launches = args.steps * len(PS)
     anneal_ms_per_launch = a_ms_max / anneal_launches
     anneal_rate = S * attempts_per_shot() / (anneal_ms_per_launch / 1e3)  # per GPU
-
-    # failure counts (logical error rate) over the timed shots, for the record
-    for i, c in enumerate(cases):
-        pass
 
     result = None
     if rank == 0:

@@ -234,3 +234,21 @@ def test_invalid_calls_fail_loudly(X, torch):
     st = lib().xzzx_anneal(code.handle, sched.handle, 1, 0, 4, 2, None, p(out["E4"]), None, None, None, None)
     assert st == XZZX_EINVAL
     torch.cuda.synchronize()
+
+
+def test_partition_independence(X, torch):
+    """One call over shots [0, n) equals two calls over [0, k) and [k, n): the
+    property that lets ranks (or serving slots) split shots freely."""
+    d, n, k, R = 11, 90, 37, 8
+    code = X.Code(d)
+    noise = X.noise_from_eta(0.19, 100)
+    sched = X.Schedule(noise, 100, 0.05, 20.0)
+    err, syn = X.sample_errors(code, noise, 42, 1000, n)
+    whole = X.decode_batch(code, noise, sched, 42, 1000, syn, R, true_errors=err, want_best_cfg=True)
+    a = X.decode_batch(code, noise, sched, 42, 1000, syn[:k].contiguous(), R, true_errors=err[:k].contiguous(),
+                       want_best_cfg=True)
+    b = X.decode_batch(code, noise, sched, 42, 1000 + k, syn[k:].contiguous(), R,
+                       true_errors=err[k:].contiguous(), want_best_cfg=True)
+    torch.cuda.synchronize()
+    for key in ("cls", "E4", "recovery", "best_cfg", "fail"):
+        assert torch.equal(whole[key], torch.cat([a[key], b[key]])), key
