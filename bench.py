@@ -154,6 +154,110 @@ def cpu_baseline(shots):
             "shots_per_s": shots / dt}
 
 
+# --------------------------------------------------------------------------- uneven batch (NEXT f1)
+UNEVEN_DS = (5, 7, 9, 13, 17, 21)
+UNEVEN_R = {5: 16, 7: 16, 9: 32, 13: 32, 17: 64, 21: 64}
+UNEVEN_N = {5: 500, 7: 500, 9: 1000, 13: 1000, 17: 2000, 21: 2000}
+UNEVEN_ETAS = (1.0, 10.0, 100.0)
+UNEVEN_PS = tuple(round(0.08 + 0.005 * k, 3) for k in range(25))   # [0.08, 0.20] on a 0.005 grid
+
+
+def uneven_segments(X, total_shots, seed, scale_shots=1.0):
+    """Shots of distances {5,7,9,13,17,21} in equal numbers; eta and p drawn per
+    shot from the seed (p on a 0.005 grid: 75 noise classes per distance);
+    shots bucketed into homogeneous segments with disjoint shot indices."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    per_d = total_shots // len(UNEVEN_DS)
+    segs, shot_base = [], 0
+    codes, scheds = {}, {}
+    for d in UNEVEN_DS:
+        eta_i = rng.integers(0, len(UNEVEN_ETAS), per_d)
+        p_i = rng.integers(0, len(UNEVEN_PS), per_d)
+        counts = np.bincount(eta_i * len(UNEVEN_PS) + p_i, minlength=len(UNEVEN_ETAS) * len(UNEVEN_PS))
+        codes[d] = X.Code(d)
+        for cls, n in enumerate(counts):
+            n = int(round(n * scale_shots))
+            if n == 0:
+                continue
+            eta, p = UNEVEN_ETAS[cls // len(UNEVEN_PS)], UNEVEN_PS[cls % len(UNEVEN_PS)]
+            noise = X.noise_from_eta(p, eta)
+            key = (d, eta, p)
+            if key not in scheds:
+                scheds[key] = X.Schedule(noise, UNEVEN_N[d], BETA0, BETA1)
+            err, syn = X.sample_errors(codes[d], noise, seed, shot_base, n)
+            segs.append(dict(code=codes[d], noise=noise, sched=scheds[key], shot0=shot_base, syndromes=syn,
+                             true_errors=err, restarts=UNEVEN_R[d]))
+            shot_base += n
+    return segs
+
+
+def run_uneven(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2509_17837_gb300 as X
+    from paper_2509_17837_gb300 import autotune
+    seed = 0xF1
+    segs = uneven_segments(X, args.uneven_shots, seed)
+    tune_segs = uneven_segments(X, args.uneven_shots, seed, scale_shots=0.125)
+    cfg, timings = autotune.tune(lambda c, o: X.Batch(tune_segs, seed, ctas_per_sm=c, order=o), tune_segs,
+                                 candidates=[(0, 0), (0, 1), (1, 0), (2, 0), (3, 0)], use_cache=False)
+    batch = X.Batch(segs, seed, ctas_per_sm=cfg[0], order=cfg[1])
+    info = batch.info()
+    stream = torch.cuda.Stream()
+    dev = torch.cuda.current_device()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        stream.synchronize()
+        ms = 0.0
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+            stream.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / steps
+
+    with torch.cuda.stream(stream):
+        ms_batched = timed(lambda: batch.run_graph(stream), args.steps, args.warmup)
+        out_b = [{k: (v.clone() if v is not None else None) for k, v in o.items()} for o in batch.outputs]
+        ms_plain = timed(lambda: batch.run(1, stream), args.steps, 1)
+    stream.synchronize()
+    same = all(torch.equal(a[k], b[k]) for a, b in zip(out_b, batch.outputs) for k in a if a[k] is not None)
+    fails = sum(int(o["fail"].sum()) for o in batch.outputs)
+    shots = info["total_shots"]
+    props = torch.cuda.get_device_properties(dev)
+    peak = props.multi_processor_count * 4 * 32 * 2070e6 / 1e12
+    att = info["move_attempts"] / (ms_batched / 1e3)
+    print(json.dumps({
+        "metric": "decoded shots/s, uneven batch (d in {5,7,9,13,17,21}, persistent launch vs one launch per distance)",
+        "value": shots / (ms_batched / 1e3), "unit": "shots/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded per-shot eta and p; library sampler)",
+        "config": {"workload": "uneven batch: %d shots, distances {5,7,9,13,17,21} equal, eta in {1,10,100}, "
+                               "p in [0.08,0.20] (0.005 grid), restarts {16,16,32,32,64,64}, sweeps "
+                               "{500,500,1000,1000,2000,2000}, linear beta 0.05->20" % shots,
+                   "segments": info["n_segments"], "chunks": info["n_chunks"],
+                   "persistent_grid": info["persistent_grid"], "autotuned_cfg": {"ctas_per_sm": cfg[0],
+                                                                                   "order": cfg[1]},
+                   "autotune_s": timings, "l2": "flushed between steps"},
+        "move_attempts_per_s": att, "plain_ms_per_step": ms_plain, "plain_shots_per_s": shots / (ms_plain / 1e3),
+        "speedup_vs_plain": ms_plain / ms_batched, "identical_outputs": bool(same),
+        "launches": {"batched_graph": info["launches_batched"], "plain": info["launches_plain"]},
+        "logical_failures": fails,
+        "roofline": {"bound": "alu", "achieved": att * I_ALG / 1e12, "peak": peak, "unit": "Tinst/s",
+                     "frac": att * I_ALG / 1e12 / peak, "traffic": None,
+                     "peak_basis": "152 SMs x 128 lanes x 2070 MHz"}}))
+
+
 # --------------------------------------------------------------------------- our arm
 def main():
     ap = argparse.ArgumentParser()
@@ -166,7 +270,11 @@ def main():
     ap.add_argument("--cpu-shots", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="d11", choices=["d11", "uneven"])
+    ap.add_argument("--uneven-shots", type=int, default=60000)
     args = ap.parse_args()
+    if args.workload == "uneven" and args.impl == "ours":
+        return run_uneven(args)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -204,6 +204,61 @@ xzzx_status xzzx_decode_batch(const xzzx_code* code, const xzzx_noise* noise, co
                               uint32_t* recovery, uint32_t* best_cfg_out, uint8_t* fail, void* workspace,
                               size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Batches of uneven segments (many distances, noise classes, schedules).   */
+/* ------------------------------------------------------------------------ */
+
+/* One homogeneous segment: n_shots syndromes of one code, noise, schedule and
+ * restart count.  Its shots are decoded exactly as xzzx_decode_batch(code,
+ * noise, sched, seed, shot0, n_shots, restarts, randomised, ...) would decode
+ * them alone.  Buffers are device memory owned by the caller and must stay
+ * valid for the life of the batch; their contents may change between runs. */
+typedef struct {
+  const xzzx_code* code;
+  const xzzx_noise* noise;
+  const xzzx_schedule* sched;
+  uint64_t shot0;
+  int32_t n_shots, restarts, randomised;
+  const uint32_t* syndromes;   /* n_shots x sw words */
+  const uint32_t* true_errors; /* n_shots x 2w words, or NULL */
+  uint8_t* cls;                /* n_shots */
+  int32_t* E4;                 /* 4 x n_shots */
+  uint32_t* recovery;          /* n_shots x 2w words */
+  uint8_t* fail;               /* n_shots, or NULL (needs true_errors) */
+} xzzx_segment;
+
+typedef struct {
+  int32_t ctas_per_sm; /* persistent grid = SMs x this; 0 = the occupancy maximum */
+  int32_t order;       /* chunk queue: 0 = longest chunks first, 1 = segment order */
+} xzzx_batch_cfg;
+
+typedef struct {
+  int32_t n_segments, n_chunks, n_distances, persistent_grid;
+  int32_t launches_batched, launches_plain;
+  size_t workspace_bytes;
+  double move_attempts;  /* per run */
+  int64_t total_shots;
+} xzzx_batch_info;
+
+typedef struct xzzx_batch xzzx_batch;
+
+/* Plan a batch (Alg. 7 applied to every segment).  Chains are cut into chunks
+ * of 128 chains of one segment.  The batch owns its descriptors and the
+ * intermediates of every segment (one device allocation).  seed keys every
+ * draw; cfg may be NULL. */
+xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t seed, const xzzx_batch_cfg* cfg,
+                              xzzx_batch** out);
+/* Decode every segment on the stream.  mode 0: one greedy launch, one
+ * persistent annealing launch whose CTAs pull chunks (longest first) from an
+ * atomic counter, one decision launch.  mode 1: the three kernels once per
+ * distance (the plain form).  Both modes give identical outputs. */
+xzzx_status xzzx_batch_run(xzzx_batch* b, int mode, void* stream);
+/* mode 0 captured into a CUDA graph on the first call (stream must not be the
+ * legacy default stream), replayed on every call. */
+xzzx_status xzzx_batch_run_graph(xzzx_batch* b, void* stream);
+xzzx_status xzzx_batch_get_info(const xzzx_batch* b, xzzx_batch_info* out);
+void xzzx_batch_destroy(xzzx_batch* b);
+
 /* Size of the scratch array built into the library for
  * xzzx_decode_batch_static (per GPU, held until the process exits). */
 #define XZZX_STATIC_SCRATCH_BYTES ((size_t)16 << 20)

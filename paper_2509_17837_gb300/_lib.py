@@ -31,6 +31,23 @@ class CodeInfo(C.Structure):
                 ("syn_words", C.c_int32), ("colour_start", C.c_int32 * 5)]
 
 
+class Segment(C.Structure):
+    _fields_ = [("code", C.c_void_p), ("noise", C.c_void_p), ("sched", C.c_void_p), ("shot0", C.c_uint64),
+                ("n_shots", C.c_int32), ("restarts", C.c_int32), ("randomised", C.c_int32),
+                ("syndromes", C.c_void_p), ("true_errors", C.c_void_p), ("cls", C.c_void_p), ("E4", C.c_void_p),
+                ("recovery", C.c_void_p), ("fail", C.c_void_p)]
+
+
+class BatchCfg(C.Structure):
+    _fields_ = [("ctas_per_sm", C.c_int32), ("order", C.c_int32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_segments", C.c_int32), ("n_chunks", C.c_int32), ("n_distances", C.c_int32),
+                ("persistent_grid", C.c_int32), ("launches_batched", C.c_int32), ("launches_plain", C.c_int32),
+                ("workspace_bytes", C.c_size_t), ("move_attempts", C.c_double), ("total_shots", C.c_int64)]
+
+
 _p = C.c_void_p
 _i = C.c_int
 _u64 = C.c_uint64
@@ -55,6 +72,11 @@ SIGNATURES = {
     "xzzx_decode_workspace_size": ([_p, _i, _i, _i, C.POINTER(C.c_size_t)], _i),
     "xzzx_decode_batch": ([_p, C.POINTER(Noise), _p, _u64, _u64, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p,
                            C.c_size_t, _p], _i),
+    "xzzx_batch_create": ([C.POINTER(Segment), _i, _u64, C.POINTER(BatchCfg), C.POINTER(_p)], _i),
+    "xzzx_batch_run": ([_p, _i, _p], _i),
+    "xzzx_batch_run_graph": ([_p, _p], _i),
+    "xzzx_batch_get_info": ([_p, C.POINTER(BatchInfo)], _i),
+    "xzzx_batch_destroy": ([_p], None),
     "xzzx_decode_batch_static": ([_p, C.POINTER(Noise), _p, _u64, _u64, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p,
                                   _p], _i),
 }

@@ -10,7 +10,7 @@ import ctypes as C
 
 import torch
 
-from ._lib import CodeInfo, Noise, call, lib
+from ._lib import BatchCfg, BatchInfo, CodeInfo, Noise, Segment, call, lib
 
 LINEAR, PAPER_LOG = 0, 1
 CONVENTION_BASELINE, CONVENTION_PAPER = 0, 1
@@ -202,3 +202,64 @@ def decode_batch(code, noise, sched, seed, shot0, syndromes, restarts, randomise
          _ptr(out["recovery"]), _ptr(out.get("best_cfg")), _ptr(out.get("fail")), _ptr(workspace),
          workspace.numel(), _stream(stream))
     return out
+
+
+class Batch:
+    """Many homogeneous segments decoded together (xzzx_batch_*).
+
+    segments: list of dicts with keys code, noise, sched, shot0, syndromes,
+    restarts, and optionally randomised (default True) and true_errors.
+    Output tensors (cls, E4, recovery, fail) are allocated per segment and
+    exposed as ``self.outputs``.  mode 0 = batched (persistent launch),
+    mode 1 = one launch per distance.
+    """
+
+    def __init__(self, segments, seed, ctas_per_sm=0, order=0):
+        self.segments = segments
+        self.outputs = []
+        arr = (Segment * len(segments))()
+        self._keep = []
+        for j, sg in enumerate(segments):
+            code, syn = sg["code"], sg["syndromes"]
+            n = syn.shape[0]
+            err = sg.get("true_errors")
+            out = dict(cls=_empty((n,), torch.uint8), E4=_empty((n, 4), torch.int32),
+                       recovery=_empty((n, 2 * code.words), torch.int32),
+                       fail=_empty((n,), torch.uint8) if err is not None else None)
+            self.outputs.append(out)
+            a = arr[j]
+            a.code, a.noise, a.sched = code.handle, C.addressof(sg["noise"]), sg["sched"].handle
+            a.shot0, a.n_shots, a.restarts = sg.get("shot0", 0), n, sg["restarts"]
+            a.randomised = int(bool(sg.get("randomised", True)))
+            a.syndromes = syn.data_ptr() if n else None
+            a.true_errors = err.data_ptr() if err is not None and n else None
+            a.cls = out["cls"].data_ptr() if n else None
+            a.E4 = out["E4"].data_ptr() if n else None
+            a.recovery = out["recovery"].data_ptr() if n else None
+            a.fail = out["fail"].data_ptr() if out["fail"] is not None and n else None
+        cfg = BatchCfg(ctas_per_sm, order)
+        h = C.c_void_p()
+        call("xzzx_batch_create", arr, len(segments), seed, C.byref(cfg), C.byref(h))
+        self._h = h
+
+    def run(self, mode=0, stream=None):
+        call("xzzx_batch_run", self._h, mode, _stream(stream))
+
+    def run_graph(self, stream):
+        call("xzzx_batch_run_graph", self._h, C.c_void_p(stream.cuda_stream))
+
+    def info(self):
+        i = BatchInfo()
+        call("xzzx_batch_get_info", self._h, C.byref(i))
+        return {k: getattr(i, k) for k, _ in BatchInfo._fields_}
+
+    def close(self):
+        if self._h:
+            lib().xzzx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,36 +1,12 @@
-// Simulated annealing of many independent chains (Alg. 2 with the Metropolis
-// step of Alg. 3), one chain per thread.
-//
-// State.  A chain lives in registers as one word per lattice row, two bits per
-// qubit (bit 2c = Z bit, bit 2c+1 = X bit of column c): 32-bit rows for d <= 15,
-// 64-bit rows up to d = 31.  The four corners of face (a, b) are then the
-// 4-bit fields at bit 2b of rows a and a+1, and applying G_f is two XORs with
-// fixed masks.
-//
-// Sweep.  Colours 0..3 in order (faces of one colour have disjoint supports,
-// so their order inside a colour does not matter).  Inside a colour the kernel
-// loops over the face columns at run time and unrolls the rows, so register
-// indices stay compile-time constants and the code stays small at any d.
-//
-// Acceptance.  An 8-bit corner signature indexes a per-sweep table of
-// (dE, A): A = T[t][dE] for dE > 0 and A = 0 otherwise, so a move is accepted
-// iff dE <= 0 or u < A.  Draws come four at a time from Philox blocks keyed by
-// (colour, column, row group, sweep, chain); a block is computed only when some
-// lane of the warp has a move with A > 0 in it, since with A = 0 the draw
-// cannot change the outcome.  The table is rebuilt for the next sweep while the
-// current one runs (double buffer, one barrier per sweep).
-//
-// Minimum tracking.  The lowest energy and its rows are recorded at the start
-// and after every colour phase (strict improvement), the rows in shared memory.
-#include <type_traits>
-
-#include "internal.h"
-#include "philox.cuh"
+// The plain annealing launch (Alg. 2 with the Metropolis step of Alg. 3):
+// one launch per distance, one chain per thread, chains of consecutive
+// (shot, restart, coset) indices.  The per-CTA work is core::anneal_cta.
+#include "anneal_core.cuh"
 
 namespace xzzx {
 namespace {
 
-constexpr int kLutN = kNumTypes * 256;
+using namespace core;
 
 struct AnnealArgs {
   PhiloxKeys keys;
@@ -49,305 +25,32 @@ struct AnnealArgs {
 };
 
 template <int D>
-struct Shape {
-  static constexpr bool kWide = 2 * D > 32;
-  using Row = typename std::conditional<kWide, uint64_t, uint32_t>::type;
-  static constexpr int kW = (D * D + 31) / 32;
-  static constexpr int kThreads = kWide ? 128 : 256;
-};
-
-template <typename Row>
-__device__ __forceinline__ uint32_t nib(Row x, uint32_t s) {
-  return (uint32_t)(x >> s) & 0xFu;
-}
-
-// Bits [start, start+len) of a bit plane (len <= 31).
-__device__ __forceinline__ uint32_t plane_field(const uint32_t* __restrict__ p, int words, int start, int len) {
-  const int wi = start >> 5, off = start & 31;
-  const uint32_t lo = p[wi];
-  const uint32_t hi = (wi + 1 < words) ? p[wi + 1] : 0u;
-  return __funnelshift_r(lo, hi, off) & ((1u << len) - 1u);
-}
-
-__device__ __forceinline__ uint64_t spread2(uint32_t v) {  // bit i -> bit 2i
-  uint64_t x = v;
-  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
-  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
-  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
-  x = (x | (x << 2)) & 0x3333333333333333ull;
-  x = (x | (x << 1)) & 0x5555555555555555ull;
-  return x;
-}
-
-__device__ __forceinline__ uint32_t gather2(uint64_t x) {  // bit 2i -> bit i
-  x &= 0x5555555555555555ull;
-  x = (x | (x >> 1)) & 0x3333333333333333ull;
-  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
-  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
-  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
-  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
-  return (uint32_t)x;
-}
-
-template <int D, typename Row>
-__device__ __forceinline__ int32_t energy_of(const Row (&R)[D], const int32_t (&W)[4]) {
-  int32_t nx = 0, ny = 0, nz = 0;
-#pragma unroll
-  for (int r = 0; r < D; ++r) {
-    const uint64_t v = (uint64_t)R[r];
-    const uint64_t z = v & 0x5555555555555555ull, x = (v >> 1) & 0x5555555555555555ull;
-    ny += __popcll(x & z);
-    nx += __popcll(x & ~z);
-    nz += __popcll(z & ~x);
-  }
-  return nx * W[2] + ny * W[3] + nz * W[1];
-}
-
-// Planar configuration (x plane then z plane) -> rows.
-template <int D, typename Row>
-__device__ __forceinline__ void load_rows(const uint32_t* __restrict__ cfg, Row (&R)[D]) {
-  constexpr int W = Shape<D>::kW;
-#pragma unroll
-  for (int r = 0; r < D; ++r) {
-    const uint32_t x = plane_field(cfg, W, r * D, D);
-    const uint32_t z = plane_field(cfg + W, W, r * D, D);
-    R[r] = (Row)(spread2(z) | (spread2(x) << 1));
-  }
-}
-
-// Rows -> planar configuration.
-template <int D, typename Row>
-__device__ __forceinline__ void store_rows(const Row (&R)[D], uint32_t* __restrict__ cfg) {
-  constexpr int W = Shape<D>::kW;
-  uint32_t px[W], pz[W];
-#pragma unroll
-  for (int j = 0; j < W; ++j) px[j] = pz[j] = 0u;
-#pragma unroll
-  for (int r = 0; r < D; ++r) {
-    const uint64_t v = (uint64_t)R[r];
-    const uint64_t fz = gather2(v), fx = gather2(v >> 1);
-    const int start = r * D, wi = start >> 5, off = start & 31;
-    pz[wi] |= (uint32_t)(fz << off);
-    px[wi] |= (uint32_t)(fx << off);
-    if (wi + 1 < W && off + D > 32) {
-      pz[wi + 1] |= (uint32_t)(fz >> (32 - off));
-      px[wi + 1] |= (uint32_t)(fx >> (32 - off));
-    }
-  }
-#pragma unroll
-  for (int j = 0; j < W; ++j) {
-    cfg[j] = px[j];
-    cfg[W + j] = pz[j];
-  }
-}
-
-// One colour phase of one sweep.
-template <int D, int C, typename Row>
-__device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint2* __restrict__ L, uint32_t t,
-                                             uint32_t c2, uint32_t c3, const PhiloxKeys& K) {
-  // Rows of this colour: a = 2j + AOFF; colour 0 ends with the bottom boundary
-  // row a = d-1, colour 3 starts with the top boundary row a = -1.
-  constexpr int NR = (C == 0 || C == 3) ? (D + 1) / 2 : (D - 1) / 2;
-  constexpr int AOFF = (C == 1) ? 1 : (C == 3) ? -1 : 0;
-  constexpr int IAOFF = (C == 1) ? 1 : 0;  // ia = (a+1)>>1 = j + IAOFF
-  constexpr int NG = (NR - 1 + IAOFF) / 4 + 1;
-  constexpr int PB = C >> 1;
-  constexpr int NCB = (D - 1) / 2;
-
-#pragma unroll 1
-  for (int jb = 0; jb < NCB; ++jb) {
-    const int b = 2 * jb + PB;
-    const uint32_t s = 2u * (uint32_t)b;
-    const uint32_t ib = (uint32_t)(b + 1) >> 1;
-    const Row m_top = (Row)0x6u << s;  // X on TL, Z on TR
-    const Row m_bot = (Row)0x9u << s;  // Z on BL, X on BR
-    uint2 e[NR];
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      const int a = 2 * j + AOFF;
-      uint32_t sig;
-      int type;
-      if (C == 3 && j == 0) {
-        type = kTop;
-        sig = nib(R[0], s) << 4;
-      } else if (C == 0 && j == NR - 1) {
-        type = kBottom;
-        sig = nib(R[D - 1], s);
-      } else {
-        type = kBulk;
-        const int a0 = a < 0 ? 0 : a;
-        const int a1 = a + 1 > D - 1 ? D - 1 : a + 1;
-        sig = nib(R[a0], s) | (nib(R[a1], s) << 4);
-      }
-      e[j] = L[type * 256 + sig];
-    }
-    uint4 r[NG];
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-      uint32_t need = 0;
-#pragma unroll
-      for (int j = 0; j < NR; ++j)
-        if (((j + IAOFF) >> 2) == g) need |= e[j].y;
-      r[g] = make_uint4(0u, 0u, 0u, 0u);
-      if (__any_sync(0xFFFFFFFFu, need != 0u))
-        r[g] = philox4x32_10(((uint32_t)C << 16) | (ib << 8) | (uint32_t)g, t, c2, c3, K);
-    }
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      const int ia = j + IAOFF;
-      const uint32_t u = lane_of(r[ia >> 2], ia & 3);
-      const int32_t dE = (int32_t)e[j].x;
-      const bool acc = (dE <= 0) | (u < e[j].y);
-      if (acc) {
-        E += dE;
-        if (C == 3 && j == 0) {
-          R[0] ^= m_bot;
-        } else if (C == 0 && j == NR - 1) {
-          R[D - 1] ^= m_top;
-        } else {
-          const int a = 2 * j + AOFF;
-          const int a0 = a < 0 ? 0 : a;
-          const int a1 = a + 1 > D - 1 ? D - 1 : a + 1;
-          R[a0] ^= m_top;
-          R[a1] ^= m_bot;
-        }
-      }
-    }
-  }
-
-  if (C == 1 || C == 2) {
-    // Boundary column: right (b = d-1: TL and BL) for colour 1, left (b = -1:
-    // TR and BR) for colour 2, over the bulk rows of the colour.
-    constexpr uint32_t sr = 2u * (uint32_t)(D - 1);
-    constexpr uint32_t ibb = (C == 1) ? (uint32_t)(D >> 1) : 0u;
-    constexpr int type = (C == 1) ? kRight : kLeft;
-    uint2 e[NR];
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      const int a = 2 * j + AOFF;
-      uint32_t sig;
-      if (C == 1)
-        sig = ((uint32_t)(R[a] >> sr) & 3u) | (((uint32_t)(R[a + 1] >> sr) & 3u) << 4);
-      else
-        sig = (((uint32_t)R[a] & 3u) << 2) | (((uint32_t)R[a + 1] & 3u) << 6);
-      e[j] = L[type * 256 + sig];
-    }
-    uint4 r[NG];
-#pragma unroll
-    for (int g = 0; g < NG; ++g) {
-      uint32_t need = 0;
-#pragma unroll
-      for (int j = 0; j < NR; ++j)
-        if (((j + IAOFF) >> 2) == g) need |= e[j].y;
-      r[g] = make_uint4(0u, 0u, 0u, 0u);
-      if (__any_sync(0xFFFFFFFFu, need != 0u))
-        r[g] = philox4x32_10(((uint32_t)C << 16) | (ibb << 8) | (uint32_t)g, t, c2, c3, K);
-    }
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-      const int ia = j + IAOFF;
-      const uint32_t u = lane_of(r[ia >> 2], ia & 3);
-      const int32_t dE = (int32_t)e[j].x;
-      const bool acc = (dE <= 0) | (u < e[j].y);
-      if (acc) {
-        E += dE;
-        const int a = 2 * j + AOFF;
-        if (C == 1) {
-          R[a] ^= (Row)2u << sr;
-          R[a + 1] ^= (Row)1u << sr;
-        } else {
-          R[a] ^= (Row)1u;
-          R[a + 1] ^= (Row)2u;
-        }
-      }
-    }
-  }
-}
-
-// Per-sweep table: entry (dE, A) for every (shape, signature).
-__device__ __forceinline__ void build_lut(uint2* __restrict__ dst, const int2* __restrict__ sig,
-                                          const uint32_t* __restrict__ Trow, int tid, int nthreads) {
-  for (int idx = tid; idx < kLutN; idx += nthreads) {
-    const int2 s = __ldg(&sig[idx]);
-    const uint32_t A = s.y >= 0 ? __ldg(&Trow[s.y]) : 0u;
-    dst[idx] = make_uint2((uint32_t)s.x, A);
-  }
-}
-
-template <int D>
 __global__ void __launch_bounds__(Shape<D>::kThreads) anneal_kernel(const __grid_constant__ AnnealArgs A) {
-  using Row = typename Shape<D>::Row;
   constexpr int NT = Shape<D>::kThreads;
   constexpr int W = Shape<D>::kW;
   extern __shared__ __align__(16) uint8_t smem[];
-  uint2* lut = reinterpret_cast<uint2*>(smem);                       // [2][kLutN]
-  Row* best_rows = reinterpret_cast<Row*>(smem + 2 * kLutN * sizeof(uint2));  // [D][NT]
-
-  const int tid = threadIdx.x;
-  const int64_t c_raw = (int64_t)blockIdx.x * NT + tid;
+  const int64_t c_raw = (int64_t)blockIdx.x * NT + threadIdx.x;
   const bool active = c_raw < A.n_chains;
   const int64_t c = active ? c_raw : A.n_chains - 1;
-  const uint64_t chain = A.chain0 + (uint64_t)c;
-  const uint32_t c2 = (uint32_t)chain;
-  const uint32_t c3 = kTagSA | ((uint32_t)(chain >> 32) << 8);
-  const int P = (int)(c & 3);
-
-  if (A.n_sweeps > 0) build_lut(lut, A.sig, A.T, tid, NT);
-
-  Row R[D];
-  load_rows<D, Row>(A.init + (size_t)(c >> 2) * 2 * W, R);
-  // Multiply by L_P: L_X = column 0 (X on even rows, Z on odd rows), L_Z = row 0
-  // (Z on even columns, X on odd columns).
-  if (P == 1 || P == 2) {
-#pragma unroll
-    for (int r = 0; r < D; ++r) R[r] ^= (Row)((r & 1) ? 1u : 2u);
-  }
-  if (P == 2 || P == 3) {
-    const uint64_t mz = 0x9999999999999999ull & ((2 * D >= 64) ? ~0ull : ((1ull << (2 * D)) - 1ull));
-    R[0] ^= (Row)mz;
-  }
-  int32_t W4[4] = {A.W[0], A.W[1], A.W[2], A.W[3]};
-  int32_t E = energy_of<D, Row>(R, W4);
-  int32_t E_best = E;
-#pragma unroll
-  for (int r = 0; r < D; ++r) best_rows[r * NT + tid] = R[r];
-  __syncthreads();
-
-  const PhiloxKeys& K = A.keys;
-  for (int t = 0; t < A.n_sweeps; ++t) {
-    const uint2* L = lut + (t & 1) * kLutN;
-    if (t + 1 < A.n_sweeps)
-      build_lut(lut + ((t + 1) & 1) * kLutN, A.sig, A.T + (size_t)(t + 1) * A.n_classes, tid, NT);
-    const uint32_t tt = (uint32_t)t;
-#define XZZX_PHASE(CC)                                        \
-  colour_phase<D, CC, Row>(R, E, L, tt, c2, c3, K);           \
-  if (E < E_best) {                                           \
-    E_best = E;                                               \
-    _Pragma("unroll") for (int r = 0; r < D; ++r) best_rows[r * NT + tid] = R[r]; \
-  }
-    XZZX_PHASE(0)
-    XZZX_PHASE(1)
-    XZZX_PHASE(2)
-    XZZX_PHASE(3)
-#undef XZZX_PHASE
-    __syncthreads();
-  }
-
-  if (!active) return;
-  A.best_E[c] = E_best;
-  if (A.final_E) A.final_E[c] = E;
-  if (A.final_cfg) store_rows<D, Row>(R, A.final_cfg + (size_t)c * 2 * W);
-  if (A.best_cfg) {
-#pragma unroll
-    for (int r = 0; r < D; ++r) R[r] = best_rows[r * NT + tid];
-    store_rows<D, Row>(R, A.best_cfg + (size_t)c * 2 * W);
-  }
+  SweepTables tab;
+  tab.T = A.T;
+  tab.sig = A.sig;
+  tab.n_sweeps = A.n_sweeps;
+  tab.n_classes = A.n_classes;
+  for (int k = 0; k < 4; ++k) tab.W[k] = A.W[k];
+  ChainOut out;
+  out.best_E = A.best_E + c;
+  out.best_cfg = A.best_cfg ? A.best_cfg + (size_t)c * 2 * W : nullptr;
+  out.final_E = A.final_E ? A.final_E + c : nullptr;
+  out.final_cfg = A.final_cfg ? A.final_cfg + (size_t)c * 2 * W : nullptr;
+  anneal_cta<D, NT>(A.init + (size_t)(c >> 2) * 2 * W, A.chain0 + (uint64_t)c, (int)(c & 3), active, out, tab,
+                    A.keys, smem);
 }
 
 template <int D>
 xzzx_status launch_d(const AnnealArgs& A, cudaStream_t stream) {
   constexpr int NT = Shape<D>::kThreads;
-  const size_t smem = 2 * kLutN * sizeof(uint2) + (size_t)D * NT * sizeof(typename Shape<D>::Row);
+  const size_t smem = smem_bytes<D, NT>();
   static bool configured = false;  // attribute is per function and device-independent
   if (!configured) {
     XZZX_CUDA_TRY(cudaFuncSetAttribute(anneal_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -1,0 +1,78 @@
+// Batched annealing kernels: a chunk of kNT chains of one segment per CTA.
+//
+// anneal_chunks_kernel<D>: one CTA per chunk of distance D (the plain,
+// one-launch-per-distance form).  anneal_persistent_kernel<DMAX>: a grid sized
+// to the GPU whose CTAs pull chunk indices from a global atomic counter and
+// run each chunk with the distance-templated core, so distances up to DMAX
+// share one launch.  Both call core::anneal_cta with the same chain ids as
+// xzzx_anneal, so results are identical to per-segment calls.
+#pragma once
+
+#include "anneal_core.cuh"
+#include "batch_internal.h"
+
+namespace xzzx {
+namespace batch {
+
+template <int D>
+__device__ __forceinline__ void run_chunk(const ChunkDev& ch, const SegDev& sg, const PhiloxKeys& K, uint8_t* smem) {
+  constexpr int W = core::Shape<D>::kW;
+  const int tid = threadIdx.x;
+  const bool active = tid < ch.n_chains;
+  const int64_t c = (int64_t)ch.first_chain + (active ? tid : ch.n_chains - 1);  // chain index in the segment
+  const uint64_t chain = sg.shot0 * (uint64_t)sg.restarts * 4u + (uint64_t)c;
+  core::SweepTables tab;
+  tab.T = ch.T;
+  tab.sig = ch.sig;
+  tab.n_sweeps = ch.n_sweeps;
+  tab.n_classes = ch.n_classes;
+  for (int k = 0; k < 4; ++k) tab.W[k] = ch.W[k];
+  core::ChainOut out;
+  out.best_E = sg.chain_E + c;
+  out.best_cfg = nullptr;
+  out.final_E = nullptr;
+  out.final_cfg = nullptr;
+  core::anneal_cta<D, kNT>(sg.init + (size_t)(c >> 2) * 2 * W, chain, (int)(c & 3), active, out, tab, K, smem);
+}
+
+template <int D>
+__global__ void __launch_bounds__(kNT) anneal_chunks_kernel(const __grid_constant__ AnnealLaunch L) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const ChunkDev ch = L.chunks[L.chunk0 + blockIdx.x];
+  run_chunk<D>(ch, L.segs[ch.seg], L.keys, smem);
+}
+
+template <int D, int DMAX>
+__device__ __forceinline__ void dispatch_chunk(const ChunkDev& ch, const SegDev& sg, const PhiloxKeys& K,
+                                               uint8_t* smem) {
+  if constexpr (D <= DMAX) {
+    if (ch.d == D) {
+      run_chunk<D>(ch, sg, K, smem);
+      return;
+    }
+    dispatch_chunk<D + 2, DMAX>(ch, sg, K, smem);
+  }
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(kNT) anneal_persistent_kernel(const __grid_constant__ AnnealLaunch L) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ int s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(L.head, 1);
+    __syncthreads();
+    const int k = s_next;
+    __syncthreads();
+    if (k >= L.n_chunks) break;
+    const ChunkDev ch = L.chunks[L.chunk0 + k];
+    dispatch_chunk<3, DMAX>(ch, L.segs[ch.seg], L.keys, smem);
+  }
+}
+
+template <int DMAX>
+constexpr size_t persistent_smem() {
+  return core::smem_bytes<DMAX, kNT>();
+}
+
+}  // namespace batch
+}  // namespace xzzx

@@ -1,12 +1,7 @@
-// Coset relabelling and decision (Alg. 7; Eqs. coset_correspondence,
-// determine_P_from_E) and the fused decoder entry point.
-//
-// One warp per shot.  Chain (i, P) belongs to coset Q_i P, where the class bits
-// of Q_i are those of R_i xor those of R_1 (commutation with L_Z and L_X is
-// linear).  Each lane folds its chains into per-coset minima of the key
-// (energy, chain index), so ties keep the lowest chain; a warp butterfly
-// reduces the four keys.
+// The coset decision launch and the fused decoder entry point (Alg. 7).
+// The per-shot work is reduce::reduce_warp (reduce_core.cuh).
 #include "internal.h"
+#include "reduce_core.cuh"
 
 namespace xzzx {
 
@@ -35,73 +30,16 @@ struct ReduceArgs {
   uint8_t* fail;
 };
 
-// Pauli index (I, X, Y, Z) <-> class bits (bit 0: anticommutes with L_Z, bit 1: with L_X).
-__device__ __forceinline__ uint32_t index_to_bits(uint32_t p) { return (0x2310u >> (4 * p)) & 3u; }
-__device__ __forceinline__ uint32_t bits_to_index(uint32_t b) { return (0x2310u >> (4 * b)) & 3u; }
-
 __global__ void __launch_bounds__(kWarps * 32) reduce_kernel(const __grid_constant__ ReduceArgs A) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
   const int64_t k = (int64_t)blockIdx.x * kWarps + warp;
   if (k >= A.n_shots) return;
   const int R = A.restarts, w = A.code.w;
-  const uint8_t* cb = A.cbits + (size_t)k * R;
-  const uint32_t q0 = cb[0] & 3u;
-  uint64_t best[4] = {~0ull, ~0ull, ~0ull, ~0ull};
-  for (int c = lane; c < 4 * R; c += 32) {
-    const uint32_t q = (cb[c >> 2] & 3u) ^ q0;
-    const uint32_t coset = bits_to_index(q ^ index_to_bits((uint32_t)(c & 3)));
-    const uint32_t e = (uint32_t)A.chain_E[(size_t)k * 4 * R + c] ^ 0x80000000u;  // order-preserving
-    const uint64_t key = ((uint64_t)e << 32) | (uint32_t)c;
-#pragma unroll
-    for (int p = 0; p < 4; ++p)
-      if (coset == (uint32_t)p && key < best[p]) best[p] = key;
-  }
-#pragma unroll
-  for (int p = 0; p < 4; ++p)
-    for (int off = 16; off > 0; off >>= 1) {
-      const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, best[p], off);
-      best[p] = o < best[p] ? o : best[p];
-    }
-  int pstar = 0;
-#pragma unroll
-  for (int p = 1; p < 4; ++p)
-    if ((best[p] >> 32) < (best[pstar] >> 32)) pstar = p;
-  if (lane == 0) {
-    A.cls[k] = (uint8_t)pstar;
-#pragma unroll
-    for (int p = 0; p < 4; ++p) A.E4[4 * k + p] = (int32_t)((uint32_t)(best[p] >> 32) ^ 0x80000000u);
-  }
-  // recovery = R_1 L_{P*}
-  const uint32_t pbits = index_to_bits((uint32_t)pstar);
-  const uint32_t* R1 = A.init + (size_t)k * R * 2 * w;
-  const uint32_t* LX = A.code.logical;
-  const uint32_t* LZ = A.code.logical + 2 * w;
-  int par_z = 0, par_x = 0;
-  for (int j = lane; j < 2 * w; j += 32) {
-    uint32_t v = R1[j];
-    if (pbits & 1u) v ^= LX[j];
-    if (pbits & 2u) v ^= LZ[j];
-    A.recovery[(size_t)k * 2 * w + j] = v;
-    if (A.true_errors) {
-      const uint32_t e = v ^ A.true_errors[(size_t)k * 2 * w + j];
-      // symplectic product with L_Z and L_X: x part meets the z part and vice versa
-      const int jj = j < w ? j + w : j - w;
-      par_z ^= __popc(e & LZ[jj]) & 1;
-      par_x ^= __popc(e & LX[jj]) & 1;
-    }
-  }
-  if (A.true_errors) {
-    for (int off = 16; off > 0; off >>= 1) {
-      par_z ^= __shfl_xor_sync(0xFFFFFFFFu, par_z, off);
-      par_x ^= __shfl_xor_sync(0xFFFFFFFFu, par_x, off);
-    }
-    if (lane == 0 && A.fail) A.fail[k] = (uint8_t)((par_z | par_x) != 0);
-  }
-  if (A.best_cfg_out && A.chain_cfg) {
-    const uint32_t bc = (uint32_t)best[pstar];
-    const uint32_t* src = A.chain_cfg + ((size_t)k * 4 * R + bc) * 2 * w;
-    for (int j = lane; j < 2 * w; j += 32) A.best_cfg_out[(size_t)k * 2 * w + j] = src[j];
-  }
+  reduce::reduce_warp(A.code, R, A.init + (size_t)k * R * 2 * w, A.cbits + (size_t)k * R, A.chain_E + (size_t)k * 4 * R,
+                      A.chain_cfg ? A.chain_cfg + (size_t)k * 4 * R * 2 * w : nullptr,
+                      A.true_errors ? A.true_errors + (size_t)k * 2 * w : nullptr, A.cls + k, A.E4 + 4 * k,
+                      A.recovery + (size_t)k * 2 * w, A.best_cfg_out ? A.best_cfg_out + (size_t)k * 2 * w : nullptr,
+                      A.fail ? A.fail + k : nullptr);
 }
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }

@@ -1,0 +1,326 @@
+// Randomised greedy matching (Algs. 5 and 6) on the GPU.
+//
+// One CTA per (shot, group of kWarps restarts); one warp per restart.  The CTA
+// first computes, in shared memory, each face's shortest distance to the open
+// boundary of its decoding graph (w(u,b) of Eq. distance_u_boundary) by
+// Bellman-Ford relaxation, and the defect list of each decoding-graph colour.
+//
+// Matching.  All candidate pairs are totally ordered by (w, key, u, v): w the
+// pair weight of Eq. distance_u_v_def_new, key a Philox draw per pair (Alg. 6)
+// or 0 (Alg. 5), u < v the stabilizer indices (0xFFFF for the virtual boundary
+// vertex).  Scanning that order and keeping pairs whose ends are free gives
+// the same matching as repeatedly matching every pair that is the best
+// remaining pair of both its ends ("locally dominant" pairs), which is what
+// the warp does, round by round, in parallel over vertices.
+//
+// Paths.  Every kept pair is joined by a canonical shortest path (a Z step
+// toward the target whenever one is needed and possible, else an X step; to
+// the boundary, the first of Z(+1,+1), Z(-1,-1), X(+1,-1), X(-1,+1) that lowers
+// the boundary distance by its weight), added modulo two into the warp's
+// configuration.  Bit 7 of cbits flags a walk that could not complete (never
+// expected on a valid code).
+#pragma once
+
+#include "internal.h"
+#include "philox.cuh"
+
+namespace xzzx {
+namespace greedy {
+
+constexpr int kWarps = 4;
+constexpr int kMaxFaces = kMaxD * kMaxD - 1;
+constexpr int kMaxColour = kMaxFaces / 2;
+constexpr int kMaxAt = (kMaxD + 1) * (kMaxD + 1);
+constexpr int kMaxWords = (kMaxD * kMaxD + 31) / 32;
+constexpr int32_t kInf = 0x3FFFFFFF;
+
+
+struct Shared {
+  int16_t fa[kMaxFaces], fb[kMaxFaces];
+  int16_t at[kMaxAt];
+  int32_t wb[kMaxFaces];
+  int16_t defects[2][kMaxColour];
+  int n_def[2];
+  uint32_t syn[(kMaxFaces + 31) / 32];
+  int16_t best[kWarps][kMaxColour + 1];
+  int16_t partner[kWarps][kMaxColour + 1];
+  uint32_t cfg[kWarps][2 * kMaxWords];
+  int walk_error[kWarps];
+};
+
+// The four edges of a face: crossed-qubit offset and step, Z edges first.
+__device__ __forceinline__ int step_a(int e) { return (e & 1) ? -1 : 1; }   // Z(+1,+1), Z(-1,-1), X(+1,-1), X(-1,+1)
+__device__ __forceinline__ int step_b(int e) { return (e == 1 || e == 2) ? -1 : 1; }
+
+struct Ctx {
+  const Shared& S;
+  int d, w;
+  int32_t Wt_x, Wt_z;
+  __device__ int face(int a, int b) const {
+    if (a < -1 || a > d - 1 || b < -1 || b > d - 1) return -1;
+    return S.at[(a + 1) * (d + 1) + (b + 1)];
+  }
+  __device__ bool qubit_in(int r, int c) const { return r >= 0 && r < d && c >= 0 && c < d; }
+  // Eq. distance_u_v_internal in rotated coordinates.
+  __device__ int32_t w_int(int u, int v) const {
+    const int su = S.fa[u] + S.fb[u], sv = S.fa[v] + S.fb[v];
+    const int du = S.fa[u] - S.fb[u], dv = S.fa[v] - S.fb[v];
+    return Wt_z * (abs(su - sv) >> 1) + Wt_x * (abs(du - dv) >> 1);
+  }
+};
+
+__device__ __forceinline__ void toggle(uint32_t* cfg, int w, int q, bool z_step) {
+  atomicXor(&cfg[(z_step ? w : 0) + (q >> 5)], 1u << (q & 31));
+}
+
+static __device__ bool walk_internal(const Ctx& X, int u, int v, uint32_t* cfg) {
+  int a = X.S.fa[u], b = X.S.fb[u];
+  const int ta = X.S.fa[v], tb = X.S.fb[v];
+  for (int guard = 0; guard < 4 * X.d * X.d + 8; ++guard) {
+    if (a == ta && b == tb) return true;
+    const int ds = (ta + tb) - (a + b), dd = (ta - tb) - (a - b);
+    if (ds != 0) {
+      const int s = ds > 0 ? 1 : -1;
+      const int na = a + s, nb = b + s, qr = max(a, na), qc = max(b, nb);
+      if (X.face(na, nb) >= 0 && X.qubit_in(qr, qc)) {
+        toggle(cfg, X.w, qr * X.d + qc, true);
+        a = na;
+        b = nb;
+        continue;
+      }
+    }
+    if (dd != 0) {
+      const int s = dd > 0 ? 1 : -1;
+      const int na = a + s, nb = b - s, qr = max(a, na), qc = max(b, nb);
+      if (X.face(na, nb) >= 0 && X.qubit_in(qr, qc)) {
+        toggle(cfg, X.w, qr * X.d + qc, false);
+        a = na;
+        b = nb;
+        continue;
+      }
+    }
+    return false;
+  }
+  return false;
+}
+
+static __device__ bool walk_boundary(const Ctx& X, int u, uint32_t* cfg) {
+  int cur = u;
+  for (int guard = 0; guard < 4 * X.d * X.d + 8; ++guard) {
+    const int a = X.S.fa[cur], b = X.S.fb[cur];
+    const int32_t here = X.S.wb[cur];
+    bool moved = false;
+    for (int e = 0; e < 4; ++e) {
+      const int na = a + step_a(e), nb = b + step_b(e);
+      const int qr = max(a, na), qc = max(b, nb);
+      if (!X.qubit_in(qr, qc)) continue;
+      const bool z_step = e < 2;
+      const int32_t w = z_step ? X.Wt_z : X.Wt_x;
+      const int nf = X.face(na, nb);
+      if (nf < 0) {
+        if (w == here) {
+          toggle(cfg, X.w, qr * X.d + qc, z_step);
+          return true;
+        }
+      } else if (X.S.wb[nf] + w == here) {
+        toggle(cfg, X.w, qr * X.d + qc, z_step);
+        cur = nf;
+        moved = true;
+        break;
+      }
+    }
+    if (!moved) return false;
+  }
+  return false;
+}
+
+// One CTA: greedy references of restarts [group*kWarps, group*kWarps + kWarps)
+// of one shot.  syn: the shot's syndrome words; init / cbits: the shot's rows
+// (restarts x 2w words, restarts bytes).
+__device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K, uint64_t shot, int group, int restarts,
+                                           int randomised, int32_t Wt_x, int32_t Wt_z, const uint32_t* __restrict__ syn,
+                                           uint32_t* __restrict__ init, uint8_t* __restrict__ cbits, Shared& S) {
+  const int d = C.d, ns = C.ns, w = C.w;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i = group * kWarps + warp;
+
+  for (int f = tid; f < ns; f += blockDim.x) {
+    S.fa[f] = C.face_a[f];
+    S.fb[f] = C.face_b[f];
+  }
+  for (int j = tid; j < (d + 1) * (d + 1); j += blockDim.x) S.at[j] = C.face_at[j];
+  for (int j = tid; j < C.sw; j += blockDim.x) S.syn[j] = syn[j];
+  __syncthreads();
+  Ctx X{S, d, w, Wt_x, Wt_z};
+
+  // Boundary distances: start from the boundary edges, relax until stable.
+  for (int f = tid; f < ns; f += blockDim.x) {
+    const int a = S.fa[f], b = S.fb[f];
+    int32_t best = kInf;
+    for (int e = 0; e < 4; ++e) {
+      const int na = a + step_a(e), nb = b + step_b(e);
+      if (!X.qubit_in(max(a, na), max(b, nb)) || X.face(na, nb) >= 0) continue;
+      best = min(best, e < 2 ? Wt_z : Wt_x);
+    }
+    S.wb[f] = best;
+  }
+  __syncthreads();
+  for (int iter = 0; iter < ns + 1; ++iter) {
+    int changed = 0;
+    for (int f = tid; f < ns; f += blockDim.x) {
+      const int a = S.fa[f], b = S.fb[f];
+      int32_t cur = S.wb[f];
+      for (int e = 0; e < 4; ++e) {
+        const int na = a + step_a(e), nb = b + step_b(e);
+        if (!X.qubit_in(max(a, na), max(b, nb))) continue;
+        const int nf = X.face(na, nb);
+        if (nf < 0) continue;
+        const int32_t cand = S.wb[nf] + (e < 2 ? Wt_z : Wt_x);
+        if (cand < cur) {
+          cur = cand;
+          changed = 1;
+        }
+      }
+      S.wb[f] = cur;
+    }
+    if (!__syncthreads_or(changed)) break;
+  }
+
+  // Defect lists of both colours, in stabilizer-index order.
+  if (warp == 0) {
+    int cnt[2] = {0, 0};
+    for (int base = 0; base < ns; base += 32) {
+      const int f = base + lane;
+      const bool on = f < ns && ((S.syn[f >> 5] >> (f & 31)) & 1);
+      const int c2 = f < ns ? C.face_c2[f] : 0;
+      for (int c = 0; c < 2; ++c) {
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, on && c2 == c);
+        if (on && c2 == c) S.defects[c][cnt[c] + __popc(m & ((1u << lane) - 1))] = (int16_t)f;
+        cnt[c] += __popc(m);
+      }
+    }
+    if (lane == 0) {
+      S.n_def[0] = cnt[0];
+      S.n_def[1] = cnt[1];
+    }
+  }
+  __syncthreads();
+  if (i >= restarts) return;
+
+  uint32_t* cfg = S.cfg[warp];
+  for (int j = lane; j < 2 * w; j += 32) cfg[j] = 0u;
+  if (lane == 0) S.walk_error[warp] = 0;
+  int16_t* best = S.best[warp];
+  int16_t* partner = S.partner[warp];
+  __syncwarp();
+
+  for (int colour = 0; colour < 2; ++colour) {
+    const int nd = S.n_def[colour];
+    const int nv = nd + (nd & 1);  // vertex nd is the virtual boundary vertex when nd is odd
+    const int16_t* D = S.defects[colour];
+    for (int x = lane; x < nv; x += 32) partner[x] = -1;
+    __syncwarp();
+    int unmatched = nv;
+    while (unmatched > 0) {
+      // Each free vertex finds its best free partner in the order (w, key, u, v).
+      for (int x = lane; x < nv; x += 32) {
+        if (partner[x] >= 0) {
+          best[x] = -1;
+          continue;
+        }
+        const bool xb = x == nd;
+        const int fx = xb ? 0 : D[x];
+        int32_t wmin = kInf;
+        for (int y = 0; y < nv; ++y) {
+          if (y == x || partner[y] >= 0) continue;
+          int32_t wxy;
+          if (xb) wxy = S.wb[D[y]];
+          else if (y == nd) wxy = S.wb[fx];
+          else wxy = min(X.w_int(fx, D[y]), S.wb[fx] + S.wb[D[y]]);
+          wmin = min(wmin, wxy);
+        }
+        int bestv = -1;
+        uint32_t bkey = 0, bu = 0, bvv = 0;
+        for (int y = 0; y < nv; ++y) {
+          if (y == x || partner[y] >= 0) continue;
+          int32_t wxy;
+          if (xb) wxy = S.wb[D[y]];
+          else if (y == nd) wxy = S.wb[fx];
+          else wxy = min(X.w_int(fx, D[y]), S.wb[fx] + S.wb[D[y]]);
+          if (wxy != wmin) continue;
+          const uint32_t sx = xb ? kBoundary : (uint32_t)fx;
+          const uint32_t sy = (y == nd) ? kBoundary : (uint32_t)D[y];
+          const uint32_t u = min(sx, sy), v = max(sx, sy);
+          uint32_t key = 0;
+          if (randomised)
+            key = philox4x32_10(u | (v << 16), (uint32_t)i, (uint32_t)shot, kTagGreedy | ((uint32_t)(shot >> 32) << 8),
+                                K).x;
+          const bool better = bestv < 0 || key < bkey || (key == bkey && (u < bu || (u == bu && v < bvv)));
+          if (better) {
+            bestv = y;
+            bkey = key;
+            bu = u;
+            bvv = v;
+          }
+        }
+        best[x] = (int16_t)bestv;
+      }
+      __syncwarp();
+      // Matching phase: reads only best[], writes only partner[].
+      int made = 0;
+      for (int x = lane; x < nv; x += 32) {
+        const int y = best[x];
+        if (y > x && best[y] == x) {
+          partner[x] = (int16_t)y;
+          partner[y] = (int16_t)x;
+          made += 2;
+        }
+      }
+      __syncwarp();
+      for (int off = 16; off > 0; off >>= 1) made += __shfl_xor_sync(0xFFFFFFFFu, made, off);
+      if (made == 0) {  // impossible for a strict total order; keep the warp from spinning
+        if (lane == 0) S.walk_error[warp] = 1;
+        break;
+      }
+      unmatched -= made;
+    }
+    // Join every kept pair.
+    for (int x = lane; x < nv; x += 32) {
+      const int y = partner[x];
+      if (y <= x || x == nd) continue;
+      bool ok;
+      const int fx = D[x];
+      if (y == nd) {
+        ok = walk_boundary(X, fx, cfg);
+      } else {
+        const int fy = D[y];
+        if (X.w_int(fx, fy) <= S.wb[fx] + S.wb[fy]) ok = walk_internal(X, fx, fy, cfg);
+        else ok = walk_boundary(X, fx, cfg) && walk_boundary(X, fy, cfg);
+      }
+      if (!ok) S.walk_error[warp] = 1;
+    }
+    __syncwarp();
+  }
+
+  // Output R_i and its commutation bits with L_Z (bit 0) and L_X (bit 1).
+  uint32_t* out = init + (size_t)i * 2 * w;
+  const uint32_t* LX = C.logical;
+  const uint32_t* LZ = C.logical + 2 * w;
+  int par_z = 0, par_x = 0;
+  for (int j = lane; j < w; j += 32) {
+    const uint32_t ex = cfg[j], ez = cfg[w + j];
+    out[j] = ex;
+    out[w + j] = ez;
+    par_z ^= __popc((ex & LZ[w + j]) ^ (ez & LZ[j])) & 1;
+    par_x ^= __popc((ex & LX[w + j]) ^ (ez & LX[j])) & 1;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    par_z ^= __shfl_xor_sync(0xFFFFFFFFu, par_z, off);
+    par_x ^= __shfl_xor_sync(0xFFFFFFFFu, par_x, off);
+  }
+  if (lane == 0)
+    cbits[i] = (uint8_t)(par_z | (par_x << 1) | (S.walk_error[warp] ? 0x80 : 0));
+}
+
+}  // namespace greedy
+}  // namespace xzzx

@@ -1,0 +1,118 @@
+"""Uneven batches: many segments with different distances, noise classes,
+schedules and restart counts in one run.  The persistent launch (mode 0), the
+one-launch-per-distance form (mode 1) and graph replays must all equal
+xzzx_decode_batch on each segment alone, bit for bit, and small segments must
+equal the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from layout import words_to_labels
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    from paper_2509_17837_gb300 import build
+    build.build()
+    import torch
+
+    import paper_2509_17837_gb300 as X
+    return X, torch
+
+
+SEG_SPECS = [  # d, p, eta, restarts, sweeps, n_shots, shot0
+    (3, 0.10, 10, 4, 40, 33, 0),
+    (5, 0.12, 1, 4, 50, 20, 1000),
+    (7, 0.18, 100, 8, 60, 9, 7),
+    (9, 0.20, 10, 8, 80, 5, 11),
+    (13, 0.15, 100, 8, 40, 3, 500),
+    (5, 0.08, 100, 6, 30, 17, 99),
+    (17, 0.15, 100, 4, 30, 2, 3),
+    (21, 0.12, 10, 4, 20, 2, 0),
+]
+
+
+def make_segments(X, torch, seed, with_errors=True):
+    segs = []
+    for d, p, eta, R, N, n, shot0 in SEG_SPECS:
+        code = X.Code(d)
+        noise = X.noise_from_eta(p, eta)
+        sched = X.Schedule(noise, N, 0.05, 20.0)
+        err, syn = X.sample_errors(code, noise, seed, shot0, n)
+        segs.append(dict(code=code, noise=noise, sched=sched, shot0=shot0, syndromes=syn, restarts=R,
+                         true_errors=err if with_errors else None))
+    return segs
+
+
+def reference_outputs(X, torch, segs, seed):
+    refs = []
+    for sg in segs:
+        refs.append(X.decode_batch(sg["code"], sg["noise"], sg["sched"], seed, sg["shot0"], sg["syndromes"],
+                                   sg["restarts"], true_errors=sg["true_errors"]))
+    torch.cuda.synchronize()
+    return refs
+
+
+def assert_same(outs, refs):
+    for j, (o, r) in enumerate(zip(outs, refs)):
+        for k in ("cls", "E4", "recovery", "fail"):
+            if r.get(k) is None:
+                continue
+            assert np.array_equal(o[k].cpu().numpy(), r[k].cpu().numpy()), (j, k)
+
+
+def test_batch_modes_match_per_segment_calls(env):
+    X, torch = env
+    seed = 0xB47C
+    segs = make_segments(X, torch, seed)
+    refs = reference_outputs(X, torch, segs, seed)
+    b = X.Batch(segs, seed)
+    info = b.info()
+    assert info["n_segments"] == len(SEG_SPECS) and info["n_distances"] == 7
+    assert info["launches_batched"] == 3 and info["launches_plain"] == 21
+    for mode in (0, 1, 0):            # a second mode-0 run reuses the reset queue
+        for o in b.outputs:
+            for t in o.values():
+                if t is not None:
+                    t.fill_(0x5A)
+        b.run(mode)
+        torch.cuda.synchronize()
+        assert_same(b.outputs, refs)
+    s = torch.cuda.Stream()
+    for _ in range(2):                # capture, then replay
+        for o in b.outputs:
+            o["cls"].fill_(7)
+        with torch.cuda.stream(s):
+            b.run_graph(s)
+        s.synchronize()
+        assert_same(b.outputs, refs)
+
+
+def test_batch_small_segments_match_oracle(env):
+    X, torch = env
+    seed = 0x0AC1E
+    segs = make_segments(X, torch, seed)[:4]
+    b = X.Batch(segs, seed, ctas_per_sm=1, order=1)
+    b.run(0)
+    torch.cuda.synchronize()
+    for sg, o, spec in zip(segs, b.outputs, SEG_SPECS):
+        d, p, eta, R, N, n, shot0 = spec
+        noise = sg["noise"]
+        pxyz = (noise.px, noise.py, noise.pz)
+        oerr, osyn = O.sample(d, pxyz, seed, shot0, n)
+        ref = O.decode(d, pxyz, noise.scale, O.LINEAR, N, 0.05, 20.0, seed, shot0, R, osyn, oerr)
+        assert np.array_equal(o["cls"].cpu().numpy(), ref["cls"])
+        assert np.array_equal(o["E4"].cpu().numpy(), ref["E4"])
+        assert np.array_equal(words_to_labels(o["recovery"].cpu().numpy(), d * d), ref["recovery"])
+        assert np.array_equal(o["fail"].cpu().numpy(), ref["fail"])
+
+
+def test_batch_rejects_bad_segments(env):
+    X, torch = env
+    from paper_2509_17837_gb300._lib import XzzxError
+    segs = make_segments(X, torch, 1)[:2]
+    segs[1]["restarts"] = 0
+    with pytest.raises(XzzxError):
+        X.Batch(segs, 1)
