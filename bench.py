@@ -258,6 +258,73 @@ def run_uneven(args):
                      "peak_basis": "152 SMs x 128 lanes x 2070 MHz"}}))
 
 
+# --------------------------------------------------------------------------- serving (NEXT f2)
+SERVE_DS = (5, 9, 13, 17, 21, 25)
+SERVE_RATES = (1e3, 3e3, 1e4, 3e4, 1e5, 3e5, 1e6)
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2509_17837_gb300 as X
+    seed, R, N = 0x5E5E, 32, 1000
+    sv = X.Server(seed, R, N, BETA0, BETA1, max_batch=args.serve_max_batch, n_slots=args.serve_slots,
+                  queue_capacity=1 << 22, hbm_budget_bytes=1 << 30)
+    noise = X.noise_from_eta(0.15, ETA)
+    cids = [sv.add_class(d, noise) for d in SERVE_DS]
+    sv.start()
+    # a pool of syndromes per distance, sampled on the device by the library
+    pool = {}
+    for d in SERVE_DS:
+        code = X.Code(d)
+        _, syn = X.sample_errors(code, noise, seed, 0, 4096, want_errors=False)
+        a = np.zeros((4096, 32), np.uint32)
+        a[:, :code.syn_words] = syn.cpu().numpy().view(np.uint32)
+        pool[d] = a
+    rng = np.random.default_rng(seed)
+    points, next_id = [], 1 << 40
+
+    def run_point(rate, n):
+        nonlocal next_id
+        which = rng.integers(0, len(SERVE_DS), n)
+        syn = np.stack([pool[SERVE_DS[w]][rng.integers(0, 4096)] for w in which])
+        ids = np.arange(next_id, next_id + n, dtype=np.uint64)
+        next_id += n
+        arrivals = np.cumsum(rng.exponential(1e6 / rate, n))
+        sv.stats(reset=True)
+        t0 = time.perf_counter()
+        sv.replay(ids, [cids[w] for w in which], syn, arrivals)
+        got = 0
+        while got < n and time.perf_counter() - t0 < 600:
+            got += len(sv.poll(cap=1 << 16, timeout_ms=100))
+        makespan = time.perf_counter() - t0
+        st = sv.stats()
+        return {"offered_req_per_s": rate, "requests": n, "completed": st["completed"],
+                "throughput_req_per_s": st["completed"] / makespan, "p50_ms": st["p50_us"] / 1e3,
+                "p99_ms": st["p99_us"] / 1e3, "max_ms": st["max_us"] / 1e3, "mean_batch": st["mean_batch"],
+                "batches": st["batches"], "rejected": st["rejected"]}
+
+    run_point(1e4, 200)  # warm-up
+    for rate in SERVE_RATES:
+        n = int(min(max(rate * args.serve_seconds, 400), args.serve_max_requests))
+        points.append(run_point(rate, n))
+    sv.close()
+    sat = max(points, key=lambda x: x["throughput_req_per_s"])
+    mean_att = np.mean([4 * R * N * (d * d - 1) for d in SERVE_DS])
+    print(json.dumps({
+        "metric": "serve p50/p99 latency vs offered load (continuous batching, mixed distances)",
+        "value": sat["throughput_req_per_s"], "unit": "req/s at saturation", "n_gpus": 1,
+        "steps": len(points), "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (library sampler, seeded; Poisson arrivals)",
+        "config": {"workload": "serving: Poisson single-shot requests, d uniform over {5,9,13,17,21,25}, eta=100, "
+                               "p=0.15, 32 restarts, 1000 sweeps, linear beta 0.05->20",
+                   "max_batch": args.serve_max_batch, "slots": args.serve_slots, "hbm_budget_bytes": 1 << 30},
+        "points": points, "saturation_move_attempts_per_s": sat["throughput_req_per_s"] * mean_att}))
+
+
 # --------------------------------------------------------------------------- our arm
 def main():
     ap = argparse.ArgumentParser()
@@ -270,11 +337,17 @@ def main():
     ap.add_argument("--cpu-shots", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="d11", choices=["d11", "uneven"])
+    ap.add_argument("--workload", default="d11", choices=["d11", "uneven", "serve"])
     ap.add_argument("--uneven-shots", type=int, default=60000)
+    ap.add_argument("--serve-seconds", type=float, default=1.0)
+    ap.add_argument("--serve-max-requests", type=int, default=6000)
+    ap.add_argument("--serve-max-batch", type=int, default=1024)
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     if args.workload == "uneven" and args.impl == "ours":
         return run_uneven(args)
+    if args.workload == "serve" and args.impl == "ours":
+        return run_serve(args)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -259,6 +259,66 @@ xzzx_status xzzx_batch_run_graph(xzzx_batch* b, void* stream);
 xzzx_status xzzx_batch_get_info(const xzzx_batch* b, xzzx_batch_info* out);
 void xzzx_batch_destroy(xzzx_batch* b);
 
+/* ------------------------------------------------------------------------ */
+/* Decode server with continuous batching.                                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  uint64_t seed;            /* keys every draw; request r uses shot index r */
+  int32_t restarts;         /* greedy restarts per request (4x chains) */
+  int32_t n_sweeps;         /* annealing sweeps */
+  int32_t sched_kind;       /* XZZX_SCHED_LINEAR or XZZX_SCHED_PAPER_LOG */
+  double beta0, beta1;      /* schedule endpoints (units of the Nishimori beta) */
+  int32_t max_batch;        /* requests per dispatched batch (<= 4096) */
+  int32_t n_slots;          /* batches in flight at once, one stream each (1..64) */
+  int32_t queue_capacity;   /* pending requests before submit returns XZZX_EBUSY */
+  size_t hbm_budget_bytes;  /* device memory for all slots, split evenly (0 = 256 MiB) */
+} xzzx_serve_cfg;
+
+typedef struct {
+  uint64_t req_id;
+  int32_t class_id, d, cls;  /* cls: decoded logical class (I=0, X=1, Y=2, Z=3) */
+  int32_t E4[4];             /* coset minimum energies */
+  uint32_t recovery[62];     /* R_1 L_cls, 2w words (w = ceil(d*d/32)) */
+  double latency_us;         /* submit to completion */
+} xzzx_result;
+
+typedef struct {
+  int64_t submitted, rejected, dispatched, completed, batches, pending, in_flight;
+  double mean_batch, p50_us, p99_us, max_us, mean_us;
+} xzzx_serve_stats;
+
+typedef struct xzzx_server xzzx_server;
+
+/* Server for single-syndrome requests (the decoder of Alg. 7 per request).
+ * Code tables, schedules and a pool of in-flight slots stay on the current
+ * device.  A dispatcher thread forms a batch whenever a slot is free, taking
+ * pending requests in arrival order (one distance group per batch) while they
+ * fit the slot's memory and the GPU's register budget, decodes it with the
+ * batched launches, and overlaps batches of different slots on the GPU.
+ * Requests that arrive while others run are admitted as slots and budget free
+ * up.  A request's result depends only on (seed, request id, class,
+ * syndrome), never on the batch it shared.  All host waits are bounded. */
+xzzx_status xzzx_serve_create(const xzzx_serve_cfg* cfg, xzzx_server** out);
+/* Register a (distance, noise) class before start; its tables stay resident. */
+xzzx_status xzzx_serve_add_class(xzzx_server* s, int d, const xzzx_noise* noise, int* class_id);
+/* Allocate the slot pool (device + pinned host) and start the dispatcher. */
+xzzx_status xzzx_serve_start(xzzx_server* s);
+/* Enqueue one request; syndrome_host: sw words of the class's code (host).
+ * XZZX_EBUSY when the queue is full (counted as rejected). */
+xzzx_status xzzx_serve_submit(xzzx_server* s, uint64_t req_id, int class_id, const uint32_t* syndrome_host);
+/* Submit n requests from a server thread at the given arrival offsets (us,
+ * ascending, relative to this call); syndromes: n x 32 words (host, copied). */
+xzzx_status xzzx_serve_replay(xzzx_server* s, int n, const uint64_t* req_ids, const int32_t* class_ids,
+                              const uint32_t* syndromes, const double* arrival_us);
+/* Move up to cap finished results to out (host); waits up to timeout_ms for
+ * the first one (XZZX_ETIMEOUT if none). */
+xzzx_status xzzx_serve_poll(xzzx_server* s, xzzx_result* out, int cap, int* n_out, int timeout_ms);
+/* Counters and latency percentiles since start or the last reset. */
+xzzx_status xzzx_serve_get_stats(xzzx_server* s, xzzx_serve_stats* out, int reset);
+/* Drain pending and in-flight requests, stop, and free everything. */
+void xzzx_serve_destroy(xzzx_server* s);
+
 /* Size of the scratch array built into the library for
  * xzzx_decode_batch_static (per GPU, held until the process exits). */
 #define XZZX_STATIC_SCRATCH_BYTES ((size_t)16 << 20)

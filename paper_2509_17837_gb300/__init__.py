@@ -7,10 +7,10 @@ built library raises.
 """
 from . import _lib
 from ._lib import XzzxError
-from .api import (CONVENTION_BASELINE, CONVENTION_PAPER, LINEAR, PAPER_LOG, Batch, Code, Schedule, anneal,
+from .api import (CONVENTION_BASELINE, CONVENTION_PAPER, LINEAR, PAPER_LOG, Batch, Code, Schedule, Server, anneal,
                   decode_batch, decode_reduce, decode_workspace_size, greedy_init, make_noise, noise_from_eta,
                   sample_errors, version)
 
-__all__ = ["Batch", "Code", "Schedule", "XzzxError", "anneal", "decode_batch", "decode_reduce", "decode_workspace_size",
+__all__ = ["Batch", "Code", "Server", "Schedule", "XzzxError", "anneal", "decode_batch", "decode_reduce", "decode_workspace_size",
            "greedy_init", "make_noise", "noise_from_eta", "sample_errors", "version", "LINEAR", "PAPER_LOG",
            "CONVENTION_BASELINE", "CONVENTION_PAPER"]

@@ -48,6 +48,25 @@ class BatchInfo(C.Structure):
                 ("workspace_bytes", C.c_size_t), ("move_attempts", C.c_double), ("total_shots", C.c_int64)]
 
 
+class ServeCfg(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("restarts", C.c_int32), ("n_sweeps", C.c_int32),
+                ("sched_kind", C.c_int32), ("beta0", C.c_double), ("beta1", C.c_double),
+                ("max_batch", C.c_int32), ("n_slots", C.c_int32), ("queue_capacity", C.c_int32),
+                ("hbm_budget_bytes", C.c_size_t)]
+
+
+class Result(C.Structure):
+    _fields_ = [("req_id", C.c_uint64), ("class_id", C.c_int32), ("d", C.c_int32), ("cls", C.c_int32),
+                ("E4", C.c_int32 * 4), ("recovery", C.c_uint32 * 62), ("latency_us", C.c_double)]
+
+
+class ServeStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("rejected", C.c_int64), ("dispatched", C.c_int64),
+                ("completed", C.c_int64), ("batches", C.c_int64), ("pending", C.c_int64),
+                ("in_flight", C.c_int64), ("mean_batch", C.c_double), ("p50_us", C.c_double),
+                ("p99_us", C.c_double), ("max_us", C.c_double), ("mean_us", C.c_double)]
+
+
 _p = C.c_void_p
 _i = C.c_int
 _u64 = C.c_uint64
@@ -77,6 +96,14 @@ SIGNATURES = {
     "xzzx_batch_run_graph": ([_p, _p], _i),
     "xzzx_batch_get_info": ([_p, C.POINTER(BatchInfo)], _i),
     "xzzx_batch_destroy": ([_p], None),
+    "xzzx_serve_create": ([C.POINTER(ServeCfg), C.POINTER(_p)], _i),
+    "xzzx_serve_add_class": ([_p, _i, C.POINTER(Noise), C.POINTER(_i)], _i),
+    "xzzx_serve_start": ([_p], _i),
+    "xzzx_serve_submit": ([_p, _u64, _i, _p], _i),
+    "xzzx_serve_replay": ([_p, _i, _p, _p, _p, _p], _i),
+    "xzzx_serve_poll": ([_p, C.POINTER(Result), _i, C.POINTER(_i), _i], _i),
+    "xzzx_serve_get_stats": ([_p, C.POINTER(ServeStats), _i], _i),
+    "xzzx_serve_destroy": ([_p], None),
     "xzzx_decode_batch_static": ([_p, C.POINTER(Noise), _p, _u64, _u64, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p,
                                   _p], _i),
 }

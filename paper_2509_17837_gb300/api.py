@@ -10,7 +10,8 @@ import ctypes as C
 
 import torch
 
-from ._lib import BatchCfg, BatchInfo, CodeInfo, Noise, Segment, call, lib
+from ._lib import (XZZX_ETIMEOUT, BatchCfg, BatchInfo, CodeInfo, Noise, Result, Segment, ServeCfg, ServeStats,
+                   XzzxError, call, lib)
 
 LINEAR, PAPER_LOG = 0, 1
 CONVENTION_BASELINE, CONVENTION_PAPER = 0, 1
@@ -256,6 +257,77 @@ class Batch:
     def close(self):
         if self._h:
             lib().xzzx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Decode server with continuous batching (xzzx_serve_*).
+
+    Requests are single syndromes (host uint32 words) of registered
+    (distance, noise) classes; results come back with their latency.
+    """
+
+    def __init__(self, seed, restarts, n_sweeps, beta0, beta1, kind=LINEAR, max_batch=256, n_slots=4,
+                 queue_capacity=1 << 20, hbm_budget_bytes=0):
+        cfg = ServeCfg(seed, restarts, n_sweeps, kind, beta0, beta1, max_batch, n_slots, queue_capacity,
+                       hbm_budget_bytes)
+        h = C.c_void_p()
+        call("xzzx_serve_create", C.byref(cfg), C.byref(h))
+        self._h = h
+        self.classes = []
+
+    def add_class(self, d, noise):
+        cid = C.c_int()
+        call("xzzx_serve_add_class", self._h, d, C.byref(noise), C.byref(cid))
+        self.classes.append((d, noise))
+        return cid.value
+
+    def start(self):
+        call("xzzx_serve_start", self._h)
+
+    def submit(self, req_id, class_id, syndrome_words):
+        import numpy as np
+        w = np.ascontiguousarray(syndrome_words, dtype=np.uint32)
+        return lib().xzzx_serve_submit(self._h, req_id, class_id, w.ctypes.data_as(C.c_void_p))
+
+    def replay(self, req_ids, class_ids, syndromes32, arrival_us):
+        import numpy as np
+        ids = np.ascontiguousarray(req_ids, dtype=np.uint64)
+        cls = np.ascontiguousarray(class_ids, dtype=np.int32)
+        syn = np.ascontiguousarray(syndromes32, dtype=np.uint32)
+        at = np.ascontiguousarray(arrival_us, dtype=np.float64)
+        assert syn.shape == (len(ids), 32)
+        call("xzzx_serve_replay", self._h, len(ids), ids.ctypes.data_as(C.c_void_p), cls.ctypes.data_as(C.c_void_p),
+             syn.ctypes.data_as(C.c_void_p), at.ctypes.data_as(C.c_void_p))
+
+    def poll(self, cap=4096, timeout_ms=100):
+        buf = (Result * cap)()
+        n = C.c_int()
+        st = lib().xzzx_serve_poll(self._h, buf, cap, C.byref(n), timeout_ms)
+        if st not in (0, XZZX_ETIMEOUT):
+            raise XzzxError(st, "xzzx_serve_poll", lib().xzzx_last_error().decode())
+        out = []
+        for i in range(n.value):
+            r = buf[i]
+            w = (r.d * r.d + 31) // 32
+            out.append(dict(req_id=r.req_id, class_id=r.class_id, d=r.d, cls=r.cls, E4=list(r.E4),
+                            recovery=list(r.recovery[:2 * w]), latency_us=r.latency_us))
+        return out
+
+    def stats(self, reset=False):
+        st = ServeStats()
+        call("xzzx_serve_get_stats", self._h, C.byref(st), int(bool(reset)))
+        return {k: getattr(st, k) for k, _ in ServeStats._fields_}
+
+    def close(self):
+        if self._h:
+            lib().xzzx_serve_destroy(self._h)
             self._h = None
 
     def __del__(self):

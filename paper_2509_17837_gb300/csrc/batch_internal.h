@@ -1,6 +1,8 @@
 // Private declarations shared by the batch translation units.
 #pragma once
 
+#include <vector>
+
 #include "internal.h"
 
 namespace xzzx {
@@ -42,12 +44,50 @@ struct AnnealLaunch {
   int* head;  // persistent queue head (reset to 0 before the launch)
 };
 
-// Per-distance chunk kernel (one CTA per chunk) and persistent kernels
-// serving every odd distance up to DMAX.
+struct DistanceRange {
+  int d;
+  int seg_begin, seg_end;        // segments [begin, end) (ordered by distance)
+  int chunk_begin, chunk_end;    // chunks_byd range
+};
+
+// Host images of a plan: segment and chunk descriptors, prefix sums and the
+// per-distance ranges.  Segment workspace pointers are assigned from a device
+// base address given to build_plan.
+struct Plan {
+  std::vector<SegDev> segs;
+  std::vector<ChunkDev> lpt, byd;
+  std::vector<int64_t> cta_prefix, shot_prefix;
+  std::vector<DistanceRange> ranges;
+  int dmax = 0;
+  double attempts = 0;
+  int64_t total_shots = 0, total_ctas = 0;
+  size_t workspace_bytes = 0;
+};
+
+// Device addresses of a plan's descriptors (one blob) and queue head.
+struct PlanDev {
+  SegDev* segs;
+  ChunkDev* lpt;
+  ChunkDev* byd;
+  int64_t* cta_prefix;
+  int64_t* shot_prefix;
+  int* head;
+};
+
+// Validate segments and build host images; workspace pointers start at
+// ws_base (may be null to size only).  order: 0 = longest chunks first.
+xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int order, char* ws_base, Plan& out);
+// Bytes of the descriptor blob and the layout of PlanDev inside it.
+size_t descriptor_bytes(const Plan& p);
+PlanDev descriptor_layout(const Plan& p, char* dev_base);
+void pack_descriptors(const Plan& p, char* host_blob);
+// Enqueue the decode of a plan (mode 0: batched, 1: one launch per distance).
+xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, int grid, int mode,
+                        cudaStream_t stream);
+xzzx_status configure_plan_kernels(int dmax, int* ctas_per_sm);
+
+// Per-distance chunk kernel (one CTA per chunk).
 xzzx_status launch_chunks(int d, const AnnealLaunch& L, cudaStream_t stream);
-xzzx_status launch_persistent(int dmax, const AnnealLaunch& L, int grid, cudaStream_t stream);
-xzzx_status persistent_occupancy(int dmax, int* ctas_per_sm);
-xzzx_status configure_kernels(int dmax);
 
 }  // namespace batch
 }  // namespace xzzx
