@@ -342,7 +342,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-max-requests", type=int, default=6000)
     ap.add_argument("--serve-max-batch", type=int, default=1024)
-    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-slots", type=int, default=8)
     args = ap.parse_args()
     if args.workload == "uneven" and args.impl == "ours":
         return run_uneven(args)

@@ -149,11 +149,15 @@ xzzx_status xzzx_schedule_table(const xzzx_schedule* sched, int* n_classes, int3
 xzzx_status xzzx_sample_errors(const xzzx_code* code, const xzzx_noise* noise, uint64_t seed, uint64_t shot0,
                                int n_shots, uint32_t* errors, uint32_t* syndromes, void* stream);
 
-/* Randomised greedy matching (Algs. 5 and 6) for every (shot, restart):
- * defects of each decoding-graph colour are paired in the order
+/* Initial references for every (shot, restart).  randomised is the init mode:
+ * 1 = greedy matching with random tie-breaking (Alg. 6), 0 = greedy matching
+ * with lexicographic ties (Alg. 5; every restart then gets the same R, as in
+ * Alg. 1), 2 = "boundary": every defect joined to the nearer boundary of its
+ * decoding graph (Sec. "Effect of initial error configuration").  Greedy
+ * matching pairs the defects of each decoding-graph colour in the order
  * (w(u,v), key, u, v), w = min(w_int, w(u,b) + w(v,b)) (Eq.
- * distance_u_v_def_new), key = a Philox draw per pair when randomised != 0 and
- * 0 otherwise, a pair kept when both ends are free; a virtual boundary vertex
+ * distance_u_v_def_new), key = a Philox draw per pair in mode 1 and 0
+ * otherwise, a pair kept when both ends are free; a virtual boundary vertex
  * joins an odd defect set; each kept pair is joined by a canonical shortest
  * path, added modulo two.  syndromes: device, n_shots x sw words.  init:
  * device, n_shots x restarts x 2w words (R_i of restart i).  cbits: device,
@@ -293,7 +297,7 @@ typedef struct xzzx_server xzzx_server;
 /* Server for single-syndrome requests (the decoder of Alg. 7 per request).
  * Code tables, schedules and a pool of in-flight slots stay on the current
  * device.  A dispatcher thread forms a batch whenever a slot is free, taking
- * pending requests in arrival order (one distance group per batch) while they
+ * pending requests in arrival order (one distance per batch) while they
  * fit the slot's memory and the GPU's register budget, decodes it with the
  * batched launches, and overlaps batches of different slots on the GPU.
  * Requests that arrive while others run are admitted as slots and budget free

@@ -19,6 +19,9 @@ from . import build as _build
 _lib = None
 
 LINEAR, PAPER_LOG = 0, 1
+INIT_GREEDY, INIT_GREEDY_RANDOM, INIT_BOUNDARY = 0, 1, 2
+ORDER_COLOUR, ORDER_RANDOM_SITE = 0, 1
+EMIN_PER_PHASE, EMIN_PER_ATTEMPT = 0, 1
 BASELINE_ETA, PAPER_ETA = 0, 1
 
 
@@ -48,6 +51,8 @@ def lib():
         L.orc_accept_threshold.restype = C.c_uint32
         L.orc_anneal_chain.argtypes = [i32, dbl, dbl, dbl, C.c_int32, i32, i32, dbl, dbl, u64, u64,
                                        p, p, p, p, p, p]
+        L.orc_anneal_chain_variant.argtypes = [i32, dbl, dbl, dbl, C.c_int32, i32, i32, dbl, dbl, u64, u64, p,
+                                               i32, i32, p, p, p, p, p]
         L.orc_decode.argtypes = [i32, dbl, dbl, dbl, C.c_int32, i32, i32, dbl, dbl, u64, u64, i32, i32,
                                  i32, p, p, p, p, p, p, p, p, p]
         L.orc_bruteforce.argtypes = [i32, dbl, dbl, dbl, C.c_int32, p, p]
@@ -219,4 +224,20 @@ def coset_energies(d, pxyz, scale, start):
     m = d * d - 1
     out = np.zeros(1 << m, np.int32)
     _check(lib().orc_coset_energies(d, *pxyz, scale, _ptr(start), _ptr(out)), "coset_energies")
+    return out
+
+
+def anneal_chain_variant(d, pxyz, scale, kind, n_sweeps, beta0, beta1, seed, chain, init, order, emin,
+                         trace=False):
+    init = np.ascontiguousarray(init, np.uint8)
+    nq = d * d
+    best, fin = np.zeros(nq, np.uint8), np.zeros(nq, np.uint8)
+    bE, fE = C.c_int32(), C.c_int32()
+    tr = np.zeros(max(n_sweeps, 1), np.int32) if trace else None
+    _check(lib().orc_anneal_chain_variant(d, *pxyz, scale, kind, n_sweeps, beta0, beta1, seed, chain, _ptr(init),
+                                          order, emin, _ptr(best), C.byref(bE), _ptr(fin), C.byref(fE), _ptr(tr)),
+           "anneal_chain_variant")
+    out = dict(best=best, best_E=bE.value, final=fin, final_E=fE.value)
+    if trace:
+        out["trace_E"] = tr[:n_sweeps]
     return out

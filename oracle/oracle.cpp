@@ -480,14 +480,31 @@ bool greedy_colour(const Code& code, const Noise& n, const std::vector<int64_t>&
   return true;
 }
 
-// Alg. 5 / Alg. 6 greedy_matching: both colours.
+// Initial reference configurations (Sec. "Effect of initial error
+// configuration on SA performance"): mode 0 = greedy matching with
+// lexicographic ties (Alg. 5; every restart gets the same R, as in Alg. 1),
+// mode 1 = greedy matching with random tie-breaking (Alg. 6), mode 2 =
+// "boundary": every defect joined to the nearer boundary of its decoding
+// graph (a shortest path to the open boundary).
+const int INIT_GREEDY = 0, INIT_GREEDY_RANDOM = 1, INIT_BOUNDARY = 2;
+
 bool greedy(const Code& code, const Noise& n, const std::vector<uint8_t>& S, uint64_t seed, uint64_t shot,
-            int restart, int randomised, std::vector<uint8_t>& R, int64_t& weight_sum) {
+            int restart, int mode, std::vector<uint8_t>& R, int64_t& weight_sum) {
   std::vector<int64_t> wb = boundary_distance(code, n);
   R.assign(code.nq, PI_);
   weight_sum = 0;
+  if (mode == INIT_BOUNDARY) {
+    for (int f = 0; f < (int)code.faces.size(); ++f) {
+      if (!S[f]) continue;
+      weight_sum += wb[f];
+      if (!walk_to_boundary(code, n, wb, f, R)) return false;
+    }
+    return true;
+  }
   for (int colour2 = 0; colour2 < 2; ++colour2)
-    if (!greedy_colour(code, n, wb, S, colour2, seed, shot, restart, randomised, R, weight_sum)) return false;
+    if (!greedy_colour(code, n, wb, S, colour2, seed, shot, restart, mode == INIT_GREEDY_RANDOM ? 1 : 0, R,
+                       weight_sum))
+      return false;
   return true;
 }
 
@@ -543,15 +560,61 @@ struct ChainResult {
   std::vector<uint8_t> best, final_cfg;
 };
 
+// Variants of Alg. 2 kept for comparison with the readings above:
+//   order 1: each sweep makes N_stab attempts on generators picked uniformly
+//            at random, as Alg. 3 states (site draw and acceptance draw from
+//            Philox(seed; k>>1, t, chain_lo, TAG_SITE|chain_hi<<8), lanes
+//            2(k&1) and 2(k&1)+1 for attempt k);
+//   emin 1:  the minimum is updated after every attempt, as Alg. 2 states.
+const int ORDER_COLOUR = 0, ORDER_RANDOM_SITE = 1;
+const int EMIN_PER_PHASE = 0, EMIN_PER_ATTEMPT = 1;
+const uint32_t TAG_SITE = 4;
+
+ChainResult anneal_chain_variant(const Code& code, const Noise& n, const Schedule& sch, uint64_t seed, uint64_t chain,
+                                 const std::vector<uint8_t>& init, int order, int emin, int32_t* trace_E);
+
 ChainResult anneal_chain(const Code& code, const Noise& n, const Schedule& sch, uint64_t seed, uint64_t chain,
                          const std::vector<uint8_t>& init, int32_t* trace_E) {
+  return anneal_chain_variant(code, n, sch, seed, chain, init, ORDER_COLOUR, EMIN_PER_PHASE, trace_E);
+}
+
+ChainResult anneal_chain_variant(const Code& code, const Noise& n, const Schedule& sch, uint64_t seed, uint64_t chain,
+                                 const std::vector<uint8_t>& init, int order, int emin, int32_t* trace_E) {
   std::vector<uint8_t> C = init;
   int64_t E = energy(n, C);
   int64_t E_best = E;
   std::vector<uint8_t> best = C;
   const uint32_t chain_lo = (uint32_t)chain, chain_hi = (uint32_t)(chain >> 32);
+  const int m = (int)code.faces.size();
   for (int t = 0; t < sch.n_sweeps; ++t) {
     double beta = beta_at(sch.kind, sch.n_sweeps, sch.beta0, sch.beta1, t);
+    if (order == ORDER_RANDOM_SITE) {
+      for (int k = 0; k < m; ++k) {
+        Draw4 r = philox4x32_10(seed, (uint32_t)(k >> 1), (uint32_t)t, chain_lo, TAG_SITE | (chain_hi << 8));
+        const int f = (int)(((uint64_t)r.v[2 * (k & 1)] * (uint64_t)m) >> 32);
+        int64_t dE = 0;
+        for (int c = 0; c < 4; ++c) {
+          int q = code.faces[f].corner[c];
+          if (q < 0) continue;
+          dE += (int64_t)n.W[C[q] ^ CORNER_PAULI[c]] - (int64_t)n.W[C[q]];
+        }
+        const bool accept = dE <= 0 || r.v[2 * (k & 1) + 1] < accept_threshold(beta, (int32_t)dE, n.scale);
+        if (accept) {
+          apply_generator(code, f, C);
+          E += dE;
+        }
+        if (emin == EMIN_PER_ATTEMPT && E < E_best) {
+          E_best = E;
+          best = C;
+        }
+      }
+      if (emin == EMIN_PER_PHASE && E < E_best) {
+        E_best = E;
+        best = C;
+      }
+      if (trace_E) trace_E[t] = (int32_t)E;
+      continue;
+    }
     for (int colour = 0; colour < 4; ++colour) {
       for (int f = code.colour_start[colour]; f < code.colour_start[colour + 1]; ++f) {
         const int ia = (code.faces[f].a + 1) >> 1, ib = (code.faces[f].b + 1) >> 1;
@@ -573,6 +636,10 @@ ChainResult anneal_chain(const Code& code, const Noise& n, const Schedule& sch, 
         if (accept) {
           apply_generator(code, f, C);
           E += dE;
+        }
+        if (emin == EMIN_PER_ATTEMPT && E < E_best) {
+          E_best = E;
+          best = C;
         }
       }
       if (E < E_best) {
@@ -814,6 +881,23 @@ int orc_anneal_chain(int d, double px, double py, double pz, int32_t scale, int 
   Schedule sch{kind, n_sweeps, beta0, beta1};
   std::vector<uint8_t> C(init, init + code.nq);
   ChainResult r = anneal_chain(code, n, sch, seed, chain, C, trace_E);
+  if (best) std::memcpy(best, r.best.data(), code.nq);
+  if (best_E) *best_E = r.best_E;
+  if (final_cfg) std::memcpy(final_cfg, r.final_cfg.data(), code.nq);
+  if (final_E) *final_E = r.final_E;
+  return 0;
+}
+
+int orc_anneal_chain_variant(int d, double px, double py, double pz, int32_t scale, int kind, int n_sweeps,
+                             double beta0, double beta1, uint64_t seed, uint64_t chain, const uint8_t* init,
+                             int order, int emin, uint8_t* best, int32_t* best_E, uint8_t* final_cfg,
+                             int32_t* final_E, int32_t* trace_E) {
+  Code code;
+  Noise n;
+  if (!get_code(d, code) || !make_noise(px, py, pz, scale, n) || n_sweeps < 0) return -1;
+  Schedule sch{kind, n_sweeps, beta0, beta1};
+  std::vector<uint8_t> C(init, init + code.nq);
+  ChainResult r = anneal_chain_variant(code, n, sch, seed, chain, C, order, emin, trace_E);
   if (best) std::memcpy(best, r.best.data(), code.nq);
   if (best_E) *best_E = r.best_E;
   if (final_cfg) std::memcpy(final_cfg, r.final_cfg.data(), code.nq);

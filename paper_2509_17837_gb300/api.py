@@ -146,7 +146,7 @@ def greedy_init(code, noise, seed, shot0, syndromes, restarts, randomised=True, 
         init = _empty((n, restarts, 2 * code.words), torch.int32)
     if cbits is None:
         cbits = _empty((n, restarts), torch.uint8)
-    call("xzzx_greedy_init", code.handle, C.byref(noise), seed, shot0, n, restarts, int(bool(randomised)),
+    call("xzzx_greedy_init", code.handle, C.byref(noise), seed, shot0, n, restarts, int(randomised),
          _ptr(syndromes), _ptr(init), _ptr(cbits), _stream(stream))
     return init, cbits
 
@@ -199,7 +199,7 @@ def decode_batch(code, noise, sched, seed, shot0, syndromes, restarts, randomise
     if workspace is None or workspace.numel() < need:
         workspace = _empty((max(need, 256),), torch.uint8)
     call("xzzx_decode_batch", code.handle, C.byref(noise), sched.handle, seed, shot0, n, restarts,
-         int(bool(randomised)), _ptr(syndromes), _ptr(true_errors), _ptr(out["cls"]), _ptr(out["E4"]),
+         int(randomised), _ptr(syndromes), _ptr(true_errors), _ptr(out["cls"]), _ptr(out["E4"]),
          _ptr(out["recovery"]), _ptr(out.get("best_cfg")), _ptr(out.get("fail")), _ptr(workspace),
          workspace.numel(), _stream(stream))
     return out
@@ -231,7 +231,7 @@ class Batch:
             a = arr[j]
             a.code, a.noise, a.sched = code.handle, C.addressof(sg["noise"]), sg["sched"].handle
             a.shot0, a.n_shots, a.restarts = sg.get("shot0", 0), n, sg["restarts"]
-            a.randomised = int(bool(sg.get("randomised", True)))
+            a.randomised = int(sg.get("randomised", 1))
             a.syndromes = syn.data_ptr() if n else None
             a.true_errors = err.data_ptr() if err is not None and n else None
             a.cls = out["cls"].data_ptr() if n else None

@@ -162,6 +162,7 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
     if (s.n_shots > 0 && (!s.syndromes || !s.cls || !s.E4 || !s.recovery))
       return fail(XZZX_EINVAL, "segment " + std::to_string(i) + ": NULL syndromes or outputs");
     if (s.fail && !s.true_errors) return fail(XZZX_EINVAL, "fail needs true_errors");
+    if (s.randomised < 0 || s.randomised > 2) return fail(XZZX_EINVAL, "init mode must be 0, 1 or 2");
   }
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return segs[x].code->d < segs[y].code->d; });
 
@@ -179,7 +180,7 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
     d.shot0 = s.shot0;
     d.n_shots = s.n_shots;
     d.restarts = s.restarts;
-    d.randomised = s.randomised ? 1 : 0;
+    d.randomised = s.randomised;
     d.greedy_groups = (s.restarts + kGreedyWarps - 1) / kGreedyWarps;
     d.Wt_x = s.noise->Wt_x;
     d.Wt_z = s.noise->Wt_z;

@@ -130,6 +130,7 @@ xzzx_status xzzx_decode_batch(const xzzx_code* code, const xzzx_noise* noise, co
       (st = check_ptr(recovery, "recovery")) || (st = check_ptr(workspace, "workspace")))
     return st;
   if (fail_out && !true_errors) return fail(XZZX_EINVAL, "fail needs true_errors");
+  if (randomised < 0 || randomised > 2) return fail(XZZX_EINVAL, "init mode must be 0, 1 or 2");
   if (((uintptr_t)workspace & 255u) != 0) return fail(XZZX_EINVAL, "workspace must be 256-byte aligned");
   const Workspace L = layout(code, n_shots, restarts, best_cfg_out != nullptr);
   if (workspace_bytes < L.total)

@@ -37,7 +37,7 @@ xzzx_status launch_greedy(const xzzx_code* code, const xzzx_noise* noise, uint64
   A.shot0 = shot0;
   A.n_shots = n_shots;
   A.restarts = restarts;
-  A.randomised = randomised ? 1 : 0;
+  A.randomised = randomised;
   A.groups = (restarts + kWarps - 1) / kWarps;
   A.Wt_x = noise->Wt_x;
   A.Wt_z = noise->Wt_z;
@@ -63,6 +63,7 @@ extern "C" xzzx_status xzzx_greedy_init(const xzzx_code* code, const xzzx_noise*
   if (!noise) return fail(XZZX_EINVAL, "noise is NULL");
   if (n_shots < 0) return fail(XZZX_EINVAL, "n_shots < 0");
   if (restarts < 1 || restarts > 65535) return fail(XZZX_EINVAL, "restarts must be in [1, 65535]");
+  if (randomised < 0 || randomised > 2) return fail(XZZX_EINVAL, "init mode must be 0, 1 or 2");
   if (noise->Wt_x <= 0 || noise->Wt_z <= 0) return fail(XZZX_EINVAL, "matching weights must be positive");
   if ((int64_t)noise->Wt_x * 4 * code->nq > kInf || (int64_t)noise->Wt_z * 4 * code->nq > kInf)
     return fail(XZZX_EINVAL, "matching weights too large for int32 path lengths");

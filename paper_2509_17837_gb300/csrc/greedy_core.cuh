@@ -28,6 +28,9 @@ namespace xzzx {
 namespace greedy {
 
 constexpr int kWarps = 4;
+// Reference modes: greedy matching with lexicographic ties (Alg. 5), with
+// random ties (Alg. 6), or every defect joined to its nearer boundary.
+constexpr int kInitGreedy = 0, kInitGreedyRandom = 1, kInitBoundary = 2;
 constexpr int kMaxFaces = kMaxD * kMaxD - 1;
 constexpr int kMaxColour = kMaxFaces / 2;
 constexpr int kMaxAt = (kMaxD + 1) * (kMaxD + 1);
@@ -134,11 +137,11 @@ static __device__ bool walk_boundary(const Ctx& X, int u, uint32_t* cfg) {
   return false;
 }
 
-// One CTA: greedy references of restarts [group*kWarps, group*kWarps + kWarps)
+// One CTA: references of restarts [group*kWarps, group*kWarps + kWarps)
 // of one shot.  syn: the shot's syndrome words; init / cbits: the shot's rows
 // (restarts x 2w words, restarts bytes).
 __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K, uint64_t shot, int group, int restarts,
-                                           int randomised, int32_t Wt_x, int32_t Wt_z, const uint32_t* __restrict__ syn,
+                                           int mode, int32_t Wt_x, int32_t Wt_z, const uint32_t* __restrict__ syn,
                                            uint32_t* __restrict__ init, uint8_t* __restrict__ cbits, Shared& S) {
   const int d = C.d, ns = C.ns, w = C.w;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -214,7 +217,14 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
   int16_t* partner = S.partner[warp];
   __syncwarp();
 
-  for (int colour = 0; colour < 2; ++colour) {
+  if (mode == kInitBoundary) {
+    // Each defect joined to the nearer boundary of its decoding graph.
+    for (int colour = 0; colour < 2; ++colour)
+      for (int x = lane; x < S.n_def[colour]; x += 32)
+        if (!walk_boundary(X, S.defects[colour][x], cfg)) S.walk_error[warp] = 1;
+    __syncwarp();
+  }
+  for (int colour = 0; colour < 2 && mode != kInitBoundary; ++colour) {
     const int nd = S.n_def[colour];
     const int nv = nd + (nd & 1);  // vertex nd is the virtual boundary vertex when nd is odd
     const int16_t* D = S.defects[colour];
@@ -252,7 +262,7 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
           const uint32_t sy = (y == nd) ? kBoundary : (uint32_t)D[y];
           const uint32_t u = min(sx, sy), v = max(sx, sy);
           uint32_t key = 0;
-          if (randomised)
+          if (mode == kInitGreedyRandom)
             key = philox4x32_10(u | (v << 16), (uint32_t)i, (uint32_t)shot, kTagGreedy | ((uint32_t)(shot >> 32) << 8),
                                 K).x;
           const bool better = bestv < 0 || key < bkey || (key == bkey && (u < bu || (u == bu && v < bvv)));

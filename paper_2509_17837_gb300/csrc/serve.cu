@@ -6,8 +6,8 @@
 // each with its own stream, descriptor area, workspace and staging buffers.
 //
 // A dispatcher thread forms a batch whenever a slot is free: it takes pending
-// requests in arrival order (within one distance group, so one annealing
-// kernel class serves the batch) while they fit the slot's memory and the
+// requests in arrival order (of one distance, so the batch's work finishes
+// together) while they fit the slot's memory and the
 // GPU's register budget, so that every admitted request's CTAs can be resident
 // at once.  The batch is decoded by the batched plan (one greedy launch, one
 // persistent annealing launch, one decision launch) between a host-to-device
@@ -83,7 +83,6 @@ struct xzzx_server {
   std::vector<xzzx::serve::Slot> slots;
   size_t slot_bytes = 0, staging_bytes = 0;
   int64_t regs_total = 0, regs_in_use = 0;
-  int64_t regs_per_cta[2] = {0, 0};  // small (d <= 15) and large groups
   bool started = false, stop = false;
   bool blocked = false;  // pending requests wait for budget freed by a completion
   std::deque<xzzx::serve::Req> pending;
@@ -208,17 +207,19 @@ void harvest(xzzx_server* sv) {
   sv->completed_slots.clear();
 }
 
-// Pick the next batch for a free slot (server lock held).  Requests of the
-// oldest pending request's group, in arrival order, while they fit.
+// Pick the next batch for a free slot (server lock held): requests of the
+// oldest pending request's distance, in arrival order, while they fit.  One
+// distance per batch keeps a batch's CTAs finishing together, so the budget
+// they hold is released without idle tails.
 bool form_batch(xzzx_server* sv, Slot& slot) {
   if (sv->pending.empty()) return false;
-  const int group = sv->classes[sv->pending.front().cls].group;
+  const int group = sv->classes[sv->pending.front().cls].d;
   size_t bytes = 4096;
   int64_t regs = 0;
   std::vector<size_t> take;
   for (size_t i = 0; i < sv->pending.size() && (int)take.size() < sv->cfg.max_batch; ++i) {
     const Class& c = sv->classes[sv->pending[i].cls];
-    if (c.group != group) continue;
+    if (c.d != group) continue;
     if (bytes + c.bytes > sv->slot_bytes) break;
     if (sv->regs_in_use + regs + c.regs > sv->regs_total && !(take.empty() && sv->regs_in_use == 0)) break;
     bytes += c.bytes;
@@ -355,23 +356,17 @@ xzzx_status xzzx_serve_start(xzzx_server* sv) {
   if (sv->classes.empty()) return fail(XZZX_EINVAL, "no classes registered");
   xzzx_status st = check_device(sv->device);
   if (st) return st;
-  // Register budget: the annealing kernel class of each group, per CTA.
-  int dmax_small = 0, dmax_large = 0;
-  for (const Class& c : sv->classes) (c.group ? dmax_large : dmax_small) = std::max(c.group ? dmax_large : dmax_small, c.d);
+  // On-chip budget: a request's CTAs take the share of an SM that the
+  // annealing kernel its distance runs (d <= 15, <= 21, <= 31) occupies.
   int regs_per_sm = 0;
   XZZX_CUDA_TRY(cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, sv->device));
   sv->regs_total = (int64_t)regs_per_sm * sv->n_sm;
-  for (int g = 0; g < 2; ++g) {
-    const int dm = g ? dmax_large : dmax_small;
-    if (dm == 0) continue;
-    int per_sm = 0;
-    if ((st = batch::configure_plan_kernels(dm, &per_sm))) return st;
-    if (per_sm < 1) per_sm = 1;
-    sv->regs_per_cta[g] = regs_per_sm / per_sm;  // share of an SM one CTA occupies
-  }
   for (Class& c : sv->classes) {
+    int per_sm = 0;
+    if ((st = batch::configure_plan_kernels(c.d, &per_sm))) return st;
+    if (per_sm < 1) per_sm = 1;
     const int64_t ctas = (4 * (int64_t)sv->cfg.restarts + batch::kNT - 1) / batch::kNT;
-    c.regs = ctas * sv->regs_per_cta[c.group];
+    c.regs = ctas * (regs_per_sm / per_sm);
   }
   const size_t budget = sv->cfg.hbm_budget_bytes ? sv->cfg.hbm_budget_bytes : ((size_t)256 << 20);
   sv->slot_bytes = budget / sv->cfg.n_slots & ~(size_t)255;

@@ -55,7 +55,7 @@ def oracle_noise(noise):
 
 @pytest.mark.parametrize("d,p,eta,n,R", [(3, 0.1, 10, 64, 8), (5, 0.2, 3, 40, 6), (11, 0.22, 100, 30, 9),
                                          (21, 0.2, 100, 6, 5), (31, 0.3, 1000, 3, 4)])
-@pytest.mark.parametrize("randomised", [1, 0])
+@pytest.mark.parametrize("randomised", [1, 0, 2])   # Alg. 6, Alg. 5, boundary initializer
 def test_greedy_parity(X, torch, d, p, eta, n, R, randomised):
     code = X.Code(d)
     noise = X.noise_from_eta(p, eta)
@@ -139,16 +139,17 @@ def test_anneal_parity_scale_4096(X, torch):
     anneal_case(X, torch, 9, 0.25, 1000, 2, 4, X.LINEAR, 40, 0.02, 30.0, scale=4096)
 
 
-def decode_case(X, torch, d, p, eta, n, R, N, b0, b1, seed, shot0=0, scale=1024, want_best=True):
+def decode_case(X, torch, d, p, eta, n, R, N, b0, b1, seed, shot0=0, scale=1024, want_best=True, mode=1):
     code = X.Code(d)
     noise = X.noise_from_eta(p, eta, 0, scale)
     pxyz = oracle_noise(noise)
     sched = X.Schedule(noise, N, b0, b1)
     oerr, osyn = O.sample(d, pxyz, seed, shot0, n)
     err, syn = X.sample_errors(code, noise, seed, shot0, n)
-    out = X.decode_batch(code, noise, sched, seed, shot0, syn, R, true_errors=err, want_best_cfg=want_best)
+    out = X.decode_batch(code, noise, sched, seed, shot0, syn, R, randomised=mode, true_errors=err,
+                         want_best_cfg=want_best)
     torch.cuda.synchronize()
-    ref = O.decode(d, pxyz, scale, O.LINEAR, N, b0, b1, seed, shot0, R, osyn, oerr)
+    ref = O.decode(d, pxyz, scale, O.LINEAR, N, b0, b1, seed, shot0, R, osyn, oerr, randomised=mode)
     assert np.array_equal(to_np(out["cls"]), ref["cls"])
     assert np.array_equal(to_np(out["E4"]), ref["E4"])
     assert np.array_equal(words_to_labels(to_np(out["recovery"]), d * d), ref["recovery"])
@@ -173,6 +174,13 @@ def test_decode_parity_d11_workload_params(X, torch, p):
 @pytest.mark.parametrize("d,n,R", [(5, 37, 7), (13, 5, 3), (25, 2, 2)])
 def test_decode_parity_other_distances(X, torch, d, n, R):
     decode_case(X, torch, d, 0.15, 100, n, R, 50, 0.05, 20.0, 77)
+
+
+@pytest.mark.parametrize("mode", [0, 2])
+def test_decode_parity_init_modes(X, torch, mode):
+    """Alg. 1 ("greedy same": deterministic greedy for every restart) and the
+    boundary initializer, end to end."""
+    decode_case(X, torch, 7, 0.15, 10, 40, 6, 80, 0.05, 20.0, 31, mode=mode)
 
 
 def test_decode_batch_equals_pipeline(X, torch):
