@@ -325,6 +325,63 @@ def run_serve(args):
         "points": points, "saturation_move_attempts_per_s": sat["throughput_req_per_s"] * mean_att}))
 
 
+# --------------------------------------------------------------------------- large distance (NEXT f4)
+LARGE_PS = (0.15, 0.18, 0.21, 0.24, 0.27, 0.30)
+
+
+def run_large(args):
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2509_17837_gb300 as X
+    d, R, N, b0, b1, scale, eta, seed = 31, 256, 10000, 0.02, 30.0, 4096, 1000.0, 0xD31
+    S = args.large_shots_per_p
+    code = X.Code(d)
+    stream = torch.cuda.current_stream()
+    cases = []
+    for i, p in enumerate(LARGE_PS):
+        noise = X.noise_from_eta(p, eta, 0, scale)
+        sched = X.Schedule(noise, N, b0, b1)
+        err, syn = X.sample_errors(code, noise, seed + i, 0, S * (args.steps + 1))
+        cases.append((noise, sched, seed + i, err, syn))
+    ws = torch.empty(X.decode_workspace_size(code, S, R), dtype=torch.uint8, device="cuda")
+    fails = 0
+
+    def step(k):
+        nonlocal fails
+        ms = 0.0
+        for noise, sched, sd, err, syn in cases:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = X.decode_batch(code, noise, sched, sd, k * S, syn[k * S:(k + 1) * S], R,
+                                 true_errors=err[k * S:(k + 1) * S], workspace=ws, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            fails += int(out["fail"].sum())
+        return ms
+
+    step(0)
+    fails = 0
+    ms = sum(step(k + 1) for k in range(args.steps)) / args.steps
+    shots = S * len(LARGE_PS)
+    att = shots * 4 * R * N * (d * d - 1) / (ms / 1e3)
+    props = torch.cuda.get_device_properties(0)
+    peak = props.multi_processor_count * 4 * 32 * 2070e6 / 1e12
+    print(json.dumps({
+        "metric": "move-attempts/s and decoded shots/s at d=31 (256 restarts, 1e4 sweeps)",
+        "value": att, "unit": "move-attempts/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (library sampler, seeded)",
+        "config": {"workload": "d=31 rotated XZZX, eta=1000, p in {0.15..0.30}, 256 restarts (1024 chains)/shot, "
+                               "1e4 sweeps, linear beta 0.02->30, scale 4096", "shots_per_p_per_step": S},
+        "shots_per_s": shots / (ms / 1e3), "logical_failures": fails, "shots_timed": shots * args.steps,
+        "roofline": {"bound": "alu", "achieved": att * I_ALG / 1e12, "peak": peak, "unit": "Tinst/s",
+                     "frac": att * I_ALG / 1e12 / peak, "traffic": None,
+                     "peak_basis": "152 SMs x 128 lanes x 2070 MHz"}}))
+
+
 # --------------------------------------------------------------------------- our arm
 def main():
     ap = argparse.ArgumentParser()
@@ -337,7 +394,8 @@ def main():
     ap.add_argument("--cpu-shots", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="d11", choices=["d11", "uneven", "serve"])
+    ap.add_argument("--workload", default="d11", choices=["d11", "uneven", "serve", "large"])
+    ap.add_argument("--large-shots-per-p", type=int, default=57)
     ap.add_argument("--uneven-shots", type=int, default=60000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-max-requests", type=int, default=6000)
@@ -348,6 +406,8 @@ def main():
         return run_uneven(args)
     if args.workload == "serve" and args.impl == "ours":
         return run_serve(args)
+    if args.workload == "large" and args.impl == "ours":
+        return run_large(args)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -20,8 +20,9 @@
 // iff dE <= 0 or u < A.  Draws come four at a time from Philox blocks keyed by
 // (colour, column, row group, sweep, chain); a block is computed only when some
 // lane of the warp has a move with A > 0 in it, since with A = 0 the draw
-// cannot change the outcome.  The table is rebuilt for the next sweep while the
-// current one runs (double buffer, one barrier per sweep).
+// cannot change the outcome.  The table is rebuilt for the next sweep after the
+// warp finishes a sweep, by the warp itself (one copy per warp), so warps
+// never wait for each other.
 //
 // Minimum tracking.  The lowest energy and its rows are recorded at the start
 // and after every colour phase (strict improvement), the rows in shared memory.
@@ -35,7 +36,7 @@
 namespace xzzx {
 namespace core {
 
-constexpr int kLutN = kNumTypes * 256;
+constexpr int kLutN = kSigTable;
 
 template <int D>
 struct Shape {
@@ -154,21 +155,17 @@ __device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
       const int a = 2 * j + AOFF;
-      uint32_t sig;
-      int type;
+      uint32_t idx;
       if (C == 3 && j == 0) {
-        type = kTop;
-        sig = nib(R[0], s) << 4;
+        idx = sig_base(kTop) + nib(R[0], s);            // BL | BR << 2
       } else if (C == 0 && j == NR - 1) {
-        type = kBottom;
-        sig = nib(R[D - 1], s);
+        idx = sig_base(kBottom) + nib(R[D - 1], s);     // TL | TR << 2
       } else {
-        type = kBulk;
         const int a0 = a < 0 ? 0 : a;
         const int a1 = a + 1 > D - 1 ? D - 1 : a + 1;
-        sig = nib(R[a0], s) | (nib(R[a1], s) << 4);
+        idx = nib(R[a0], s) | (nib(R[a1], s) << 4);     // TL | TR << 2 | BL << 4 | BR << 6
       }
-      e[j] = L[type * 256 + sig];
+      e[j] = L[idx];
     }
     uint4 r[NG];
 #pragma unroll
@@ -209,17 +206,16 @@ __device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint
     // TR and BR) for colour 2, over the bulk rows of the colour.
     constexpr uint32_t sr = 2u * (uint32_t)(D - 1);
     constexpr uint32_t ibb = (C == 1) ? (uint32_t)(D >> 1) : 0u;
-    constexpr int type = (C == 1) ? kRight : kLeft;
     uint2 e[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
       const int a = 2 * j + AOFF;
-      uint32_t sig;
-      if (C == 1)
-        sig = ((uint32_t)(R[a] >> sr) & 3u) | (((uint32_t)(R[a + 1] >> sr) & 3u) << 4);
-      else
-        sig = (((uint32_t)R[a] & 3u) << 2) | (((uint32_t)R[a + 1] & 3u) << 6);
-      e[j] = L[type * 256 + sig];
+      uint32_t idx;
+      if (C == 1)  // TL | BL << 2
+        idx = sig_base(kRight) + (((uint32_t)(R[a] >> sr) & 3u) | (((uint32_t)(R[a + 1] >> sr) & 3u) << 2));
+      else  // TR | BR << 2
+        idx = sig_base(kLeft) + (((uint32_t)R[a] & 3u) | (((uint32_t)R[a + 1] & 3u) << 2));
+      e[j] = L[idx];
     }
     uint4 r[NG];
 #pragma unroll
@@ -253,16 +249,16 @@ __device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint
   }
 }
 
-// Per-sweep table: entry (dE, A) for every (shape, signature).
-__device__ __forceinline__ void build_lut(uint2* __restrict__ dst, const int2* __restrict__ sig,
-                                          const uint32_t* __restrict__ Trow, int tid, int nthreads) {
-  for (int idx = tid; idx < kLutN; idx += nthreads) {
-    const int2 s = __ldg(&sig[idx]);
+// Per-sweep table: entry (dE, A) for every compact signature, built by one
+// warp into its own copy from the CTA's static (dE, class) table.
+__device__ __forceinline__ void build_lut_warp(uint2* __restrict__ dst, const int2* __restrict__ sig_static,
+                                               const uint32_t* __restrict__ Trow, int lane) {
+  for (int idx = lane; idx < kLutN; idx += 32) {
+    const int2 s = sig_static[idx];
     const uint32_t A = s.y >= 0 ? __ldg(&Trow[s.y]) : 0u;
     dst[idx] = make_uint2((uint32_t)s.x, A);
   }
 }
-
 
 // Tables a CTA needs: per-sweep thresholds, signature table and qubit weights.
 struct SweepTables {
@@ -280,9 +276,12 @@ struct ChainOut {
   uint32_t* final_cfg;
 };
 
+// Shared memory: the static (dE, class) table, one per-sweep table per warp,
+// and the minimum-energy rows of every chain.
 template <int D, int NT>
 __host__ __device__ constexpr size_t smem_bytes() {
-  return 2 * kLutN * sizeof(uint2) + (size_t)D * NT * sizeof(typename Shape<D>::Row);
+  return kLutN * sizeof(int2) + (size_t)(NT / 32) * kLutN * sizeof(uint2) +
+         (size_t)D * NT * sizeof(typename Shape<D>::Row);
 }
 
 // Anneal one chain per thread; every thread of the CTA must call this (it
@@ -295,14 +294,18 @@ __device__ __forceinline__ void anneal_cta(const uint32_t* __restrict__ init, ui
                                            uint8_t* smem) {
   using Row = typename Shape<D>::Row;
   constexpr int W = Shape<D>::kW;
-  uint2* lut = reinterpret_cast<uint2*>(smem);                                 // [2][kLutN]
-  Row* best_rows = reinterpret_cast<Row*>(smem + 2 * kLutN * sizeof(uint2));  // [D][NT]
-  const int tid = threadIdx.x;
+  int2* sig_static = reinterpret_cast<int2*>(smem);                                     // [kLutN]
+  uint2* lut_all = reinterpret_cast<uint2*>(smem + kLutN * sizeof(int2));               // [NT/32][kLutN]
+  Row* best_rows = reinterpret_cast<Row*>(smem + kLutN * sizeof(int2) + (NT / 32) * kLutN * sizeof(uint2));
+  const int tid = threadIdx.x, lane = tid & 31;
+  uint2* L = lut_all + (tid >> 5) * kLutN;  // this warp's table
   const uint32_t c2 = (uint32_t)chain;
   const uint32_t c3 = kTagSA | ((uint32_t)(chain >> 32) << 8);
   const int n_sweeps = tab.n_sweeps;
 
-  if (n_sweeps > 0) build_lut(lut, tab.sig, tab.T, tid, NT);
+  for (int idx = tid; idx < kLutN; idx += NT) sig_static[idx] = __ldg(&tab.sig[idx]);
+  __syncthreads();  // the only CTA barrier: warps then sweep independently
+  if (n_sweeps > 0) build_lut_warp(L, sig_static, tab.T, lane);
 
   Row R[D];
   load_rows<D, Row>(init, R);
@@ -321,12 +324,9 @@ __device__ __forceinline__ void anneal_cta(const uint32_t* __restrict__ init, ui
   int32_t E_best = E;
 #pragma unroll
   for (int r = 0; r < D; ++r) best_rows[r * NT + tid] = R[r];
-  __syncthreads();
+  __syncwarp();
 
   for (int t = 0; t < n_sweeps; ++t) {
-    const uint2* L = lut + (t & 1) * kLutN;
-    if (t + 1 < n_sweeps)
-      build_lut(lut + ((t + 1) & 1) * kLutN, tab.sig, tab.T + (size_t)(t + 1) * tab.n_classes, tid, NT);
     const uint32_t tt = (uint32_t)t;
 #define XZZX_PHASE(CC)                                                              \
   colour_phase<D, CC, Row>(R, E, L, tt, c2, c3, K);                                 \
@@ -339,7 +339,11 @@ __device__ __forceinline__ void anneal_cta(const uint32_t* __restrict__ init, ui
     XZZX_PHASE(2)
     XZZX_PHASE(3)
 #undef XZZX_PHASE
-    __syncthreads();
+    if (t + 1 < n_sweeps) {  // next sweep's thresholds, once every lane is done with these
+      __syncwarp();
+      build_lut_warp(L, sig_static, tab.T + (size_t)(t + 1) * tab.n_classes, lane);
+      __syncwarp();
+    }
   }
 
   if (!active) return;

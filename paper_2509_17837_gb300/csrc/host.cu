@@ -288,32 +288,31 @@ xzzx_status xzzx_make_schedule(const xzzx_noise* noise, int kind, int n_sweeps, 
   s->beta0 = beta0;
   s->beta1 = beta1;
   s->noise = *noise;
-  // Energy change of each generator shape for each 8-bit corner signature:
-  // X flips the x bit of TL and BR, Z flips the z bit of TR and BL.
+  // Energy change of each generator shape for each corner signature (compact
+  // table: bulk by its 8-bit signature TL|TR<<2|BL<<4|BR<<6, weight-2 shapes
+  // by their two present corners): X flips the x bit of TL and BR, Z flips
+  // the z bit of TR and BL.
   const int flip[4] = {2, 1, 1, 2};
-  s->sig_dE.assign(kNumTypes * 256, 0);
-  s->sig_class.assign(kNumTypes * 256, -1);
+  s->sig_dE.assign(kSigTable, 0);
+  s->sig_class.assign(kSigTable, -1);
   std::set<int32_t> positive;
   for (int y = 0; y < kNumTypes; ++y) {
-    for (int sig = 0; sig < 256; ++sig) {
-      bool valid = true;
+    int present[4], np = 0;
+    for (int k = 0; k < 4; ++k)
+      if ((kCornerMask[y] >> k) & 1) present[np++] = k;
+    for (int code = 0; code < (1 << (2 * np)); ++code) {
       int64_t dE = 0;
-      for (int k = 0; k < 4; ++k) {
-        const int lab = (sig >> (2 * k)) & 3;
-        if (!((kCornerMask[y] >> k) & 1)) {
-          if (lab) valid = false;
-          continue;
-        }
-        dE += (int64_t)noise->W[lab ^ flip[k]] - (int64_t)noise->W[lab];
+      for (int j = 0; j < np; ++j) {
+        const int lab = (code >> (2 * j)) & 3;
+        dE += (int64_t)noise->W[lab ^ flip[present[j]]] - (int64_t)noise->W[lab];
       }
-      if (!valid) continue;
-      s->sig_dE[y * 256 + sig] = (int32_t)dE;
+      s->sig_dE[sig_base(y) + code] = (int32_t)dE;
       if (dE > 0) positive.insert((int32_t)dE);
     }
   }
   s->dE_class.assign(positive.begin(), positive.end());
   s->n_classes = (int)s->dE_class.size();
-  for (int i = 0; i < kNumTypes * 256; ++i) {
+  for (int i = 0; i < kSigTable; ++i) {
     const int32_t dE = s->sig_dE[i];
     if (dE > 0)
       s->sig_class[i] = (int32_t)(std::lower_bound(s->dE_class.begin(), s->dE_class.end(), dE) - s->dE_class.begin());
@@ -324,8 +323,8 @@ xzzx_status xzzx_make_schedule(const xzzx_noise* noise, int kind, int n_sweeps, 
     for (int k = 0; k < s->n_classes; ++k)
       s->T[(size_t)t * s->n_classes + k] = threshold_of(beta, s->dE_class[k], noise->scale);
   }
-  std::vector<int2> sig(kNumTypes * 256);
-  for (int i = 0; i < kNumTypes * 256; ++i) sig[i] = make_int2(s->sig_dE[i], s->sig_class[i]);
+  std::vector<int2> sig(kSigTable);
+  for (int i = 0; i < kSigTable; ++i) sig[i] = make_int2(s->sig_dE[i], s->sig_class[i]);
   if (!has_device()) {  // host tables only; launches with this handle are refused
     *out = s;
     return XZZX_OK;

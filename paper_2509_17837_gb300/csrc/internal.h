@@ -38,6 +38,11 @@ constexpr uint32_t kBoundary = 0xFFFFu;
 // faces, by which corners exist.  Signature bits: TL 0-1, TR 2-3, BL 4-5, BR 6-7.
 enum FaceType { kBulk = 0, kTop = 1, kBottom = 2, kLeft = 3, kRight = 4, kNumTypes = 5 };
 constexpr int kCornerMask[kNumTypes] = {0xF, 0xC, 0x3, 0xA, 0x5};  // bit k = corner k present
+// Compact signature table: the 256 bulk signatures, then 16 entries per
+// weight-2 shape indexed by its two present corners (the first present corner
+// in bits 0-1, the second in bits 2-3).
+constexpr int kSigTable = 256 + 4 * 16;
+__host__ __device__ constexpr int sig_base(int type) { return type == kBulk ? 0 : 256 + 16 * (type - 1); }
 
 // Round keys of Philox4x32-10 for one seed, in kernel-parameter space.
 struct PhiloxKeys {
@@ -79,10 +84,10 @@ struct xzzx_schedule {
   int n_classes = 0;
   std::vector<int32_t> dE_class;        // positive dE values, ascending
   std::vector<uint32_t> T;              // n_sweeps x n_classes
-  std::vector<int32_t> sig_dE;          // kNumTypes x 256
-  std::vector<int32_t> sig_class;       // kNumTypes x 256, class index or -1 (dE <= 0)
+  std::vector<int32_t> sig_dE;          // kSigTable entries
+  std::vector<int32_t> sig_class;       // kSigTable entries, class index or -1 (dE <= 0)
   uint32_t* d_T = nullptr;              // device copy of T (at least one row)
-  int2* d_sig = nullptr;                // device (dE, class) per type x signature
+  int2* d_sig = nullptr;                // device (dE, class) per compact signature
 };
 
 namespace xzzx {
