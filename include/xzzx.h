@@ -180,6 +180,14 @@ xzzx_status xzzx_anneal(const xzzx_code* code, const xzzx_schedule* sched, uint6
                         int n_shots, int restarts, const uint32_t* init, int32_t* best_E, uint32_t* best_cfg,
                         int32_t* final_E, uint32_t* final_cfg, void* stream);
 
+/* xzzx_anneal with one warp per chain instead of one thread: the lanes take a
+ * colour's faces in parallel (rows in shared memory, accepted moves applied
+ * with shared atomics), cutting each chain's sequential work up to 32-fold
+ * for latency-bound use.  Same arguments, draws and results as xzzx_anneal. */
+xzzx_status xzzx_anneal_warp(const xzzx_code* code, const xzzx_schedule* sched, uint64_t seed, uint64_t shot0,
+                             int n_shots, int restarts, const uint32_t* init, int32_t* best_E, uint32_t* best_cfg,
+                             int32_t* final_E, uint32_t* final_cfg, void* stream);
+
 /* Coset relabelling and decision (Alg. 7, Eqs. coset_correspondence,
  * determine_P_from_E): chain (i, P) belongs to coset Q_i P with
  * [L_Q] = [R_i R_1]; E4[P] is the minimum over coset P; cls = argmin with
@@ -255,7 +263,8 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
 /* Decode every segment on the stream.  mode 0: one greedy launch, one
  * persistent annealing launch whose CTAs pull chunks (longest first) from an
  * atomic counter, one decision launch.  mode 1: the three kernels once per
- * distance (the plain form).  Both modes give identical outputs. */
+ * distance (the plain form).  mode 2: as mode 1 with one warp per chain
+ * (xzzx_anneal_warp).  All modes give identical outputs. */
 xzzx_status xzzx_batch_run(xzzx_batch* b, int mode, void* stream);
 /* mode 0 captured into a CUDA graph on the first call (stream must not be the
  * legacy default stream), replayed on every call. */
@@ -277,6 +286,10 @@ typedef struct {
   int32_t n_slots;          /* batches in flight at once, one stream each (1..64) */
   int32_t queue_capacity;   /* pending requests before submit returns XZZX_EBUSY */
   size_t hbm_budget_bytes;  /* device memory for all slots, split evenly (0 = 256 MiB) */
+  int32_t warp_max_requests;/* a batch of at most this many requests anneals with one warp per
+                               chain (lower latency) while the warps of all batches doing so
+                               stay within 16 per SM; otherwise one thread per chain, which
+                               has the higher throughput (0 = 16, -1 = never) */
 } xzzx_serve_cfg;
 
 typedef struct {

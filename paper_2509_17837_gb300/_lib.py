@@ -52,7 +52,7 @@ class ServeCfg(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("restarts", C.c_int32), ("n_sweeps", C.c_int32),
                 ("sched_kind", C.c_int32), ("beta0", C.c_double), ("beta1", C.c_double),
                 ("max_batch", C.c_int32), ("n_slots", C.c_int32), ("queue_capacity", C.c_int32),
-                ("hbm_budget_bytes", C.c_size_t)]
+                ("hbm_budget_bytes", C.c_size_t), ("warp_max_requests", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -87,6 +87,7 @@ SIGNATURES = {
     "xzzx_sample_errors": ([_p, C.POINTER(Noise), _u64, _u64, _i, _p, _p, _p], _i),
     "xzzx_greedy_init": ([_p, C.POINTER(Noise), _u64, _u64, _i, _i, _i, _p, _p, _p, _p], _i),
     "xzzx_anneal": ([_p, _p, _u64, _u64, _i, _i, _p, _p, _p, _p, _p, _p], _i),
+    "xzzx_anneal_warp": ([_p, _p, _u64, _u64, _i, _i, _p, _p, _p, _p, _p, _p], _i),
     "xzzx_decode_reduce": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
     "xzzx_decode_workspace_size": ([_p, _i, _i, _i, C.POINTER(C.c_size_t)], _i),
     "xzzx_decode_batch": ([_p, C.POINTER(Noise), _p, _u64, _u64, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p,

@@ -152,7 +152,7 @@ def greedy_init(code, noise, seed, shot0, syndromes, restarts, randomised=True, 
 
 
 def anneal(code, sched, seed, shot0, init, want_cfg=True, want_final=False, best_E=None, best_cfg=None,
-           final_E=None, final_cfg=None, stream=None):
+           final_E=None, final_cfg=None, stream=None, per_warp=False):
     n, restarts = init.shape[0], init.shape[1]
     chains = n * restarts * 4
     if best_E is None:
@@ -163,7 +163,8 @@ def anneal(code, sched, seed, shot0, init, want_cfg=True, want_final=False, best
         final_E = final_E if final_E is not None else _empty((n, restarts, 4), torch.int32)
         final_cfg = final_cfg if final_cfg is not None else _empty((n, restarts, 4, 2 * code.words), torch.int32)
     assert best_E.numel() == chains
-    call("xzzx_anneal", code.handle, sched.handle, seed, shot0, n, restarts, _ptr(init), _ptr(best_E),
+    call("xzzx_anneal_warp" if per_warp else "xzzx_anneal", code.handle, sched.handle, seed, shot0, n, restarts,
+         _ptr(init), _ptr(best_E),
          _ptr(best_cfg), _ptr(final_E), _ptr(final_cfg), _stream(stream))
     return dict(best_E=best_E, best_cfg=best_cfg, final_E=final_E, final_cfg=final_cfg)
 
@@ -274,9 +275,9 @@ class Server:
     """
 
     def __init__(self, seed, restarts, n_sweeps, beta0, beta1, kind=LINEAR, max_batch=256, n_slots=4,
-                 queue_capacity=1 << 20, hbm_budget_bytes=0):
+                 queue_capacity=1 << 20, hbm_budget_bytes=0, warp_max_requests=0):
         cfg = ServeCfg(seed, restarts, n_sweeps, kind, beta0, beta1, max_batch, n_slots, queue_capacity,
-                       hbm_budget_bytes)
+                       hbm_budget_bytes, warp_max_requests)
         h = C.c_void_p()
         call("xzzx_serve_create", C.byref(cfg), C.byref(h))
         self._h = h

@@ -7,7 +7,8 @@
 //   mode 0 (batched): one greedy launch over every (segment, shot, restart
 //          group), one persistent annealing launch whose CTAs pull chunks,
 //          longest first, from an atomic counter, and one decision launch;
-//   mode 1 (plain):   the same three kernels once per distance.
+//   mode 1 (plain):   the same three kernels once per distance;
+//   mode 2 (latency): as mode 1 with one warp per chain (colour-parallel lanes).
 // Every chain uses the chain id it would get from xzzx_decode_batch on its
 // segment alone, so both modes, and per-segment calls, agree bit for bit.
 //
@@ -170,6 +171,7 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
   P.segs.resize(n_segs);
   P.cta_prefix.assign(n_segs + 1, 0);
   P.shot_prefix.assign(n_segs + 1, 0);
+  P.chain_prefix.assign(n_segs + 1, 0);
   size_t ws = 0;
   std::vector<ChunkDev> chunks;
   for (int j = 0; j < n_segs; ++j) {
@@ -196,8 +198,14 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
     ws = align256(ws + n * R);
     d.chain_E = (int32_t*)(ws_base ? ws_base + ws : nullptr);
     ws = align256(ws + sizeof(int32_t) * n * R * 4);
+    d.T = s.sched->d_T;
+    d.sig = s.sched->d_sig;
+    d.n_sweeps = s.sched->n_sweeps;
+    d.n_classes = s.sched->n_classes;
+    for (int k = 0; k < 4; ++k) d.W[k] = s.sched->noise.W[k];
     P.cta_prefix[j + 1] = P.cta_prefix[j] + (int64_t)s.n_shots * d.greedy_groups;
     P.shot_prefix[j + 1] = P.shot_prefix[j] + s.n_shots;
+    P.chain_prefix[j + 1] = P.chain_prefix[j] + (int64_t)s.n_shots * s.restarts * 4;
     P.dmax = std::max(P.dmax, s.code->d);
     const int64_t nch = (int64_t)s.n_shots * s.restarts * 4;
     if (nch > 0x7FFFFFFFll) return fail(XZZX_EINVAL, "segment too large");
@@ -242,7 +250,7 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
 
 namespace {
 struct BlobLayout {
-  size_t segs, lpt, byd, cta, shot, head, total;
+  size_t segs, lpt, byd, cta, shot, chain, head, total;
 };
 BlobLayout blob_layout(const Plan& p) {
   BlobLayout L;
@@ -252,7 +260,8 @@ BlobLayout blob_layout(const Plan& p) {
   L.byd = align256(L.lpt + sizeof(ChunkDev) * nc);
   L.cta = align256(L.byd + sizeof(ChunkDev) * nc);
   L.shot = align256(L.cta + sizeof(int64_t) * p.cta_prefix.size());
-  L.head = align256(L.shot + sizeof(int64_t) * p.shot_prefix.size());
+  L.chain = align256(L.shot + sizeof(int64_t) * p.shot_prefix.size());
+  L.head = align256(L.chain + sizeof(int64_t) * p.chain_prefix.size());
   L.total = align256(L.head + sizeof(int));
   return L;
 }
@@ -268,6 +277,7 @@ PlanDev descriptor_layout(const Plan& p, char* base) {
   d.byd = (ChunkDev*)(base + L.byd);
   d.cta_prefix = (int64_t*)(base + L.cta);
   d.shot_prefix = (int64_t*)(base + L.shot);
+  d.chain_prefix = (int64_t*)(base + L.chain);
   d.head = (int*)(base + L.head);
   return d;
 }
@@ -282,6 +292,7 @@ void pack_descriptors(const Plan& p, char* blob) {
   }
   std::memcpy(blob + L.cta, p.cta_prefix.data(), sizeof(int64_t) * p.cta_prefix.size());
   std::memcpy(blob + L.shot, p.shot_prefix.data(), sizeof(int64_t) * p.shot_prefix.size());
+  std::memcpy(blob + L.chain, p.chain_prefix.data(), sizeof(int64_t) * p.chain_prefix.size());
 }
 
 xzzx_status configure_plan_kernels(int dmax, int* ctas_per_sm) {
@@ -320,8 +331,19 @@ xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, in
     if ((st = run_greedy(p, d, K, p.cta_prefix[r.seg_begin], p.cta_prefix[r.seg_end] - p.cta_prefix[r.seg_begin],
                          stream)))
       return st;
-    if ((st = launch_chunks(r.d, anneal_launch(d, K, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin), stream)))
+    if (mode == 2) {
+      WarpLaunch W;
+      W.keys = K;
+      W.segs = d.segs;
+      W.chain_prefix = d.chain_prefix;
+      W.n_segs = (int)p.segs.size();
+      W.chain0 = p.chain_prefix[r.seg_begin];
+      W.n_chains = p.chain_prefix[r.seg_end] - p.chain_prefix[r.seg_begin];
+      if ((st = launch_warp_chains(r.d, W, stream))) return st;
+    } else if ((st = launch_chunks(r.d, anneal_launch(d, K, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin),
+                                   stream))) {
       return st;
+    }
     if ((st = run_reduce(p, d, p.shot_prefix[r.seg_begin], p.shot_prefix[r.seg_end] - p.shot_prefix[r.seg_begin],
                          stream)))
       return st;
@@ -409,7 +431,8 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
 
 xzzx_status xzzx_batch_run(xzzx_batch* b, int mode, void* stream) {
   if (!b) return fail(XZZX_EINVAL, "batch is NULL");
-  if (mode != 0 && mode != 1) return fail(XZZX_EINVAL, "mode must be 0 (batched) or 1 (one launch per distance)");
+  if (mode < 0 || mode > 2)
+    return fail(XZZX_EINVAL, "mode must be 0 (batched), 1 (one launch per distance) or 2 (one warp per chain)");
   xzzx_status st = check_device(b->device);
   if (st) return st;
   return launch_plan(b->plan, b->dev, b->keys, b->grid, mode, (cudaStream_t)stream);

@@ -25,6 +25,11 @@ struct SegDev {
   uint32_t* init;     // workspace: n_shots x restarts x 2w words
   uint8_t* cbits;     // workspace: n_shots x restarts
   int32_t* chain_E;   // workspace: n_shots x restarts x 4
+  // schedule (also carried by every chunk of the segment)
+  const uint32_t* T;
+  const int2* sig;
+  int n_sweeps, n_classes;
+  int32_t W[4];
 };
 
 // kNT consecutive chains of one segment (one CTA's work).
@@ -56,7 +61,7 @@ struct DistanceRange {
 struct Plan {
   std::vector<SegDev> segs;
   std::vector<ChunkDev> lpt, byd;
-  std::vector<int64_t> cta_prefix, shot_prefix;
+  std::vector<int64_t> cta_prefix, shot_prefix, chain_prefix;
   std::vector<DistanceRange> ranges;
   int dmax = 0;
   double attempts = 0;
@@ -71,6 +76,7 @@ struct PlanDev {
   ChunkDev* byd;
   int64_t* cta_prefix;
   int64_t* shot_prefix;
+  int64_t* chain_prefix;
   int* head;
 };
 
@@ -81,13 +87,24 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
 size_t descriptor_bytes(const Plan& p);
 PlanDev descriptor_layout(const Plan& p, char* dev_base);
 void pack_descriptors(const Plan& p, char* host_blob);
-// Enqueue the decode of a plan (mode 0: batched, 1: one launch per distance).
+// Enqueue the decode of a plan (mode 0: batched, 1: one launch per distance,
+// 2: one launch per distance with one warp per chain).
 xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, int grid, int mode,
                         cudaStream_t stream);
 xzzx_status configure_plan_kernels(int dmax, int* ctas_per_sm);
 
 // Per-distance chunk kernel (one CTA per chunk).
 xzzx_status launch_chunks(int d, const AnnealLaunch& L, cudaStream_t stream);
+
+// Per-distance warp-per-chain kernel over the chains [chain0, chain0 + n).
+struct WarpLaunch {
+  PhiloxKeys keys;
+  const SegDev* segs;
+  const int64_t* chain_prefix;
+  int n_segs;
+  int64_t chain0, n_chains;
+};
+xzzx_status launch_warp_chains(int d, const WarpLaunch& L, cudaStream_t stream);
 
 }  // namespace batch
 }  // namespace xzzx

@@ -10,7 +10,9 @@
 // together) while they fit the slot's memory and the
 // GPU's register budget, so that every admitted request's CTAs can be resident
 // at once.  The batch is decoded by the batched plan (one greedy launch, one
-// persistent annealing launch, one decision launch) between a host-to-device
+// persistent annealing launch, one decision launch; small batches on a lightly
+// loaded GPU anneal with one warp per chain instead, for latency) between a
+// host-to-device
 // copy of the syndromes and a device-to-host copy of the results; batches in
 // different slots overlap on the GPU.  A host callback on the slot's stream
 // stamps the completion time.  Requests that arrive while others run are
@@ -62,6 +64,8 @@ struct Slot {
   char* host_in = nullptr;   // pinned: descriptors + syndromes
   char* host_out = nullptr;  // pinned: results
   bool busy = false;
+  bool warp_mode = false;  // anneal this batch with one warp per chain
+  int64_t warps = 0;       // warps it occupies while it does
   int64_t regs = 0;
   std::vector<Req> reqs;
   size_t off_out = 0, out_stride = 0;
@@ -83,6 +87,7 @@ struct xzzx_server {
   std::vector<xzzx::serve::Slot> slots;
   size_t slot_bytes = 0, staging_bytes = 0;
   int64_t regs_total = 0, regs_in_use = 0;
+  int64_t warp_inflight = 0;  // warps of batches annealing one warp per chain
   bool started = false, stop = false;
   bool blocked = false;  // pending requests wait for budget freed by a completion
   std::deque<xzzx::serve::Req> pending;
@@ -171,7 +176,7 @@ xzzx_status issue(xzzx_server* sv, Slot& slot) {
   XZZX_CUDA_TRY(cudaMemcpyAsync(slot.dev, slot.host_in, desc, cudaMemcpyHostToDevice, slot.stream));
   XZZX_CUDA_TRY(cudaMemcpyAsync(slot.dev + o_syn, slot.host_in + o_syn, syn_bytes, cudaMemcpyHostToDevice,
                                 slot.stream));
-  if ((st = launch_plan(plan, pd, sv->keys, (int)plan.lpt.size(), 0, slot.stream))) return st;
+  if ((st = launch_plan(plan, pd, sv->keys, (int)plan.lpt.size(), slot.warp_mode ? 2 : 0, slot.stream))) return st;
   XZZX_CUDA_TRY(cudaMemcpyAsync(slot.host_out, slot.dev + o_out, out_bytes, cudaMemcpyDeviceToHost, slot.stream));
   XZZX_CUDA_TRY(cudaLaunchHostFunc(slot.stream, on_complete, &slot));
   return XZZX_OK;
@@ -199,8 +204,10 @@ void harvest(xzzx_server* sv) {
       ++sv->completed;
     }
     sv->regs_in_use -= s.regs;
+    sv->warp_inflight -= s.warps;
     s.reqs.clear();
     s.regs = 0;
+    s.warps = 0;
     s.busy = false;
   }
   if (!sv->completed_slots.empty()) sv->cv_done.notify_all();
@@ -242,6 +249,15 @@ bool form_batch(xzzx_server* sv, Slot& slot) {
   sv->pending.swap(rest);
   slot.reqs.swap(reqs);
   slot.regs = regs;
+  // A small batch anneals one warp per chain while the warps of all batches
+  // doing so stay within 16 per SM: a lightly loaded GPU has the room, and
+  // each chain's sequential work is shorter.  Past that the batch runs one
+  // thread per chain, which has the higher throughput.
+  const int warp_max = sv->cfg.warp_max_requests == 0 ? 16 : sv->cfg.warp_max_requests;
+  const int64_t warps = (int64_t)slot.reqs.size() * 4 * sv->cfg.restarts;
+  slot.warp_mode = (int)slot.reqs.size() <= warp_max && sv->warp_inflight + warps <= (int64_t)sv->n_sm * 16;
+  slot.warps = slot.warp_mode ? warps : 0;
+  sv->warp_inflight += slot.warps;
   slot.busy = true;
   sv->regs_in_use += regs;
   sv->dispatched += (int64_t)slot.reqs.size();
@@ -283,8 +299,10 @@ void dispatcher_main(xzzx_server* sv) {
         sv->sticky = st;
         sv->sticky_msg = std::string("dispatch failed: ") + xzzx_last_error();
         sv->regs_in_use -= s.regs;
+        sv->warp_inflight -= s.warps;
         s.reqs.clear();
         s.regs = 0;
+        s.warps = 0;
         s.busy = false;
         break;
       }

@@ -72,7 +72,7 @@ def test_batch_modes_match_per_segment_calls(env):
     info = b.info()
     assert info["n_segments"] == len(SEG_SPECS) and info["n_distances"] == 7
     assert info["launches_batched"] == 3 and info["launches_plain"] == 21
-    for mode in (0, 1, 0):            # a second mode-0 run reuses the reset queue
+    for mode in (0, 1, 2, 0):         # a second mode-0 run reuses the reset queue
         for o in b.outputs:
             for t in o.values():
                 if t is not None:

@@ -91,7 +91,7 @@ def test_greedy_parity_dense_random_syndromes(X, torch, d, density):
             assert np.array_equal(words_to_labels(init[s, i], d * d), ref)
 
 
-def anneal_case(X, torch, d, p, eta, n, R, kind, N, b0, b1, seed=3, shot0=11, scale=1024):
+def anneal_case(X, torch, d, p, eta, n, R, kind, N, b0, b1, seed=3, shot0=11, scale=1024, per_warp=False):
     code = X.Code(d)
     noise = X.noise_from_eta(p, eta, 0, scale)
     pxyz = oracle_noise(noise)
@@ -100,7 +100,7 @@ def anneal_case(X, torch, d, p, eta, n, R, kind, N, b0, b1, seed=3, shot0=11, sc
     refs = np.array([[O.greedy(d, pxyz, scale, seed, shot0 + s, i, 1, osyn[s])[0] for i in range(R)]
                      for s in range(n)])
     init = gpu_words(torch, labels_to_words(refs))
-    out = X.anneal(code, sched, seed, shot0, init, want_cfg=True, want_final=True)
+    out = X.anneal(code, sched, seed, shot0, init, want_cfg=True, want_final=True, per_warp=per_warp)
     torch.cuda.synchronize()
     bE, fE = to_np(out["best_E"]), to_np(out["final_E"])
     bc = words_to_labels(to_np(out["best_cfg"]), d * d)
@@ -124,10 +124,17 @@ def test_anneal_parity_every_distance(X, torch, d):
     anneal_case(X, torch, d, 0.18, 30, 3, 5, X.LINEAR, 24 if d < 21 else 10, 0.1, 6.0)
 
 
+@pytest.mark.parametrize("d", [3, 5, 7, 11, 13, 17, 21, 25, 31])
+def test_anneal_warp_per_chain_parity(X, torch, d):
+    """One warp per chain (colour-parallel lanes) equals the oracle bit for bit."""
+    anneal_case(X, torch, d, 0.18, 30, 3, 5, X.LINEAR, 24 if d < 21 else 10, 0.1, 6.0, per_warp=True)
+
+
 @pytest.mark.parametrize("kind,N,b0,b1", [(0, 0, 0.1, 1.0), (0, 1, 0.4, 9.0), (0, 3, 0.0, 0.0),
                                           (0, 12, 1e6, 1e6), (1, 30, 0.9, 1.0), (0, 60, 0.05, 20.0)])
 def test_anneal_parity_schedules(X, torch, kind, N, b0, b1):
     anneal_case(X, torch, 7, 0.2, 100, 4, 3, kind, N, b0, b1)
+    anneal_case(X, torch, 9, 0.2, 100, 2, 3, kind, N, b0, b1, per_warp=True)
 
 
 def test_anneal_parity_large_chain_ids(X, torch):

@@ -32,8 +32,11 @@ def env():
 
 
 def make_server(X, **kw):
+    # batches of at most 4 requests anneal one warp per chain, larger ones one
+    # thread per chain: the probe below runs alone in the first mode and in
+    # the mix mostly in the second
     sv = X.Server(SEED, R, N, B0, B1, max_batch=kw.get("max_batch", 16), n_slots=kw.get("n_slots", 3),
-                  queue_capacity=kw.get("queue_capacity", 100000))
+                  queue_capacity=kw.get("queue_capacity", 100000), warp_max_requests=4)
     ids = []
     for d, p, eta in CLASSES:
         ids.append(sv.add_class(d, X.noise_from_eta(p, eta)))
