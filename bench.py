@@ -31,7 +31,11 @@ sys.path.insert(0, ROOT)
 
 D, ETA, PS, RESTARTS, SWEEPS, BETA0, BETA1, SCALE = 11, 100.0, (0.10, 0.13, 0.16, 0.19, 0.22), 64, 1000, 0.05, 20.0, 1024
 SEED = 0xD11
-I_ALG = 30  # integer instructions per move attempt in the algorithmic count (see DESIGN.md)
+I_ALG = 30  # integer instructions per move attempt in the algorithmic count
+# DRAM bytes (read + write) per chain of anneal_kernel<11>, from one ncu
+# capture of the current kernel (128,000 chains, 1.5373e6 B): each chain reads
+# its 32-byte reference (shared by its four cosets) and writes 4 bytes.
+ANNEAL_DRAM_BYTES_PER_CHAIN = 1.5373e6 / 128000
 
 
 def workload_config(shots_per_p, world):
@@ -532,7 +536,7 @@ def main():
             "kernel_ms_per_step": {"greedy": g_ms / args.steps, "anneal": a_ms / args.steps,
                                    "reduce": r_ms / args.steps},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": ANNEAL_DRAM_BYTES_PER_CHAIN * S * RESTARTS * 4,
                          "kernel": "anneal_kernel<11>", "I_alg_per_attempt": I_ALG,
                          "peak_basis": "%d SMs x 4 SMSP x 32 lanes x %.0f MHz (median SM clock sampled in the timed region)"
                                        % (n_sm, f_mhz)},
