@@ -66,6 +66,14 @@ def max_over_ranks(values, dist, device):
     return [float(x) for x in t]
 
 
+def sum_over_ranks(values, dist, device):
+    """Element-wise SUM over ranks (counts such as logical failures)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t]
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -146,6 +154,32 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------- CPU baseline (oracle)
+def _oracle_worker(args):
+    shot0, shots = args
+    import oracle as O
+    pxyz = O.noise_from_eta(0.16, ETA)
+    err, syn = O.sample(D, pxyz, SEED, shot0, shots)
+    O.decode(D, pxyz, SCALE, O.LINEAR, SWEEPS, BETA0, BETA1, SEED, shot0, RESTARTS, syn, err)
+    return shots
+
+
+def cpu_baseline_all_cores(shots_per_core):
+    """The oracle as independent single-threaded processes on every host core,
+    over disjoint shot ranges (spawned, so no CUDA state is inherited)."""
+    import multiprocessing as mp
+    n = os.cpu_count() or 1
+    import oracle.build
+    oracle.build.build()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(n) as pool:
+        t0 = time.perf_counter()
+        done = sum(pool.map(_oracle_worker, [(1000 + k * shots_per_core, shots_per_core) for k in range(n)]))
+        dt = time.perf_counter() - t0
+    return {"value": attempts_per_shot() * done / dt, "unit": "move-attempts/s", "cores": n, "kind": "oracle",
+            "sample": "%d processes x %d shots of d=11 p=0.16, %.1f s wall" % (n, shots_per_core, dt),
+            "shots_per_s": done / dt}
+
+
 def cpu_baseline(shots):
     import oracle as O
     pxyz = O.noise_from_eta(0.16, ETA)
@@ -339,6 +373,7 @@ def run_large(args):
     import __graft_entry__
     __graft_entry__.build()
     import paper_2509_17837_gb300 as X
+    from paper_2509_17837_gb300 import stats
     d, R, N, b0, b1, scale, eta, seed = 31, 256, 10000, 0.02, 30.0, 4096, 1000.0, 0xD31
     S = args.large_shots_per_p
     code = X.Code(d)
@@ -381,6 +416,7 @@ def run_large(args):
         "config": {"workload": "d=31 rotated XZZX, eta=1000, p in {0.15..0.30}, 256 restarts (1024 chains)/shot, "
                                "1e4 sweeps, linear beta 0.02->30, scale 4096", "shots_per_p_per_step": S},
         "shots_per_s": shots / (ms / 1e3), "logical_failures": fails, "shots_timed": shots * args.steps,
+        "logical_error_rate_all_p": stats.ler_record(None, fails, shots * args.steps),
         "roofline": {"bound": "alu", "achieved": att * I_ALG / 1e12, "peak": peak, "unit": "Tinst/s",
                      "frac": att * I_ALG / 1e12 / peak, "traffic": None,
                      "peak_basis": "152 SMs x 128 lanes x 2070 MHz"}}))
@@ -433,6 +469,7 @@ def main():
     import __graft_entry__
     __graft_entry__.build()
     import paper_2509_17837_gb300 as X
+    from paper_2509_17837_gb300 import stats
 
     def barrier():
         if world > 1:
@@ -494,10 +531,15 @@ def main():
     t_wall = time.perf_counter()
     all_ev = []
     fails = [0] * len(PS)
+    fail_hist = []
     for k in range(args.warmup, n_steps):
         flush.fill_(k & 0xFF)  # evict L2 between steps (outside the per-step events)
         all_ev.append(step(k, True))
+        fail_hist.append([o["fail"] for o in outs])  # each step's reduce returns fresh tensors
     barrier()
+    fail_dev = [sum(int(h[i].sum()) for h in fail_hist) for i in range(len(PS))]
+    if world > 1:
+        fail_dev = [int(f) for f in sum_over_ranks([float(f) for f in fail_dev], dist, dev)]
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop() if rank == 0 else None
     g_ms = a_ms = r_ms = 0.0
@@ -541,6 +583,7 @@ def main():
                          "peak_basis": "%d SMs x 4 SMSP x 32 lanes x %.0f MHz (median SM clock sampled in the timed region)"
                                        % (n_sm, f_mhz)},
             "clocks": clocks, "gpu_launches": 3 * len(PS) * args.steps,
+            "logical_error_rates": [stats.ler_record(p, f, S * args.steps * world) for p, f in zip(PS, fail_dev)],
             "wall_s_timed_region": wall,
         }
     # ---------------------------------------------------------------- e2e through the C ABI, host buffers
@@ -581,6 +624,7 @@ def main():
                                      "host syndromes/errors copied in, classes and failure flags copied out" % S}
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args.cpu_shots)
+        result["cpu_baseline_all_cores"] = cpu_baseline_all_cores(max(1, args.cpu_shots // 2))
     if rank == 0:
         print(json.dumps(result))
     if world > 1:

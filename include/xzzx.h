@@ -188,6 +188,23 @@ xzzx_status xzzx_anneal_warp(const xzzx_code* code, const xzzx_schedule* sched, 
                              int n_shots, int restarts, const uint32_t* init, int32_t* best_E, uint32_t* best_cfg,
                              int32_t* final_E, uint32_t* final_cfg, void* stream);
 
+/* Annealing in the literal forms of Alg. 2 and Alg. 3, for comparison with
+ * the colour sweep of xzzx_anneal.  order 0: each sweep visits the
+ * generators in stabilizer-index order with the draws of xzzx_anneal;
+ * order 1: each sweep makes N_stab attempts on generators drawn uniformly at
+ * random (Alg. 3), attempt k of sweep t taking its site draw u and
+ * acceptance draw from lanes 2(k&1) and 2(k&1)+1 of Philox(seed; k>>1, t,
+ * chain_lo, 4 | chain_hi<<8), the site being floor(u * N_stab / 2^32).
+ * emin 0: the minimum is taken at the start and after every colour phase
+ * (order 0) or every sweep (order 1); emin 1: after every attempt as well
+ * (Alg. 2).  With order 0 and emin 0 the results equal xzzx_anneal.  One
+ * chain per thread, rows in shared memory (slower than xzzx_anneal).  Other
+ * arguments as xzzx_anneal; XZZX_EINVAL for an order or emin outside {0, 1}. */
+xzzx_status xzzx_anneal_variant(const xzzx_code* code, const xzzx_schedule* sched, uint64_t seed, uint64_t shot0,
+                                int n_shots, int restarts, int order, int emin, const uint32_t* init,
+                                int32_t* best_E, uint32_t* best_cfg, int32_t* final_E, uint32_t* final_cfg,
+                                void* stream);
+
 /* Coset relabelling and decision (Alg. 7, Eqs. coset_correspondence,
  * determine_P_from_E): chain (i, P) belongs to coset Q_i P with
  * [L_Q] = [R_i R_1]; E4[P] is the minimum over coset P; cls = argmin with

@@ -88,6 +88,7 @@ SIGNATURES = {
     "xzzx_greedy_init": ([_p, C.POINTER(Noise), _u64, _u64, _i, _i, _i, _p, _p, _p, _p], _i),
     "xzzx_anneal": ([_p, _p, _u64, _u64, _i, _i, _p, _p, _p, _p, _p, _p], _i),
     "xzzx_anneal_warp": ([_p, _p, _u64, _u64, _i, _i, _p, _p, _p, _p, _p, _p], _i),
+    "xzzx_anneal_variant": ([_p, _p, _u64, _u64, _i, _i, _i, _i, _p, _p, _p, _p, _p, _p], _i),
     "xzzx_decode_reduce": ([_p, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p], _i),
     "xzzx_decode_workspace_size": ([_p, _i, _i, _i, C.POINTER(C.c_size_t)], _i),
     "xzzx_decode_batch": ([_p, C.POINTER(Noise), _p, _u64, _u64, _i, _i, _i, _p, _p, _p, _p, _p, _p, _p, _p,

@@ -15,6 +15,8 @@ from ._lib import (XZZX_ETIMEOUT, BatchCfg, BatchInfo, CodeInfo, Noise, Result, 
 
 LINEAR, PAPER_LOG = 0, 1
 CONVENTION_BASELINE, CONVENTION_PAPER = 0, 1
+ORDER_COLOUR, ORDER_RANDOM_SITE = 0, 1       # sweep order of xzzx_anneal_variant
+EMIN_PER_PHASE, EMIN_PER_ATTEMPT = 0, 1      # when the minimum is taken
 
 
 def _ptr(t):
@@ -152,7 +154,10 @@ def greedy_init(code, noise, seed, shot0, syndromes, restarts, randomised=True, 
 
 
 def anneal(code, sched, seed, shot0, init, want_cfg=True, want_final=False, best_E=None, best_cfg=None,
-           final_E=None, final_cfg=None, stream=None, per_warp=False):
+           final_E=None, final_cfg=None, stream=None, per_warp=False, order=ORDER_COLOUR, emin=EMIN_PER_PHASE):
+    """Alg. 2 for every chain.  per_warp selects xzzx_anneal_warp; a non-default
+    order (ORDER_RANDOM_SITE) or emin (EMIN_PER_ATTEMPT) selects
+    xzzx_anneal_variant, the literal forms of Alg. 2 / Alg. 3."""
     n, restarts = init.shape[0], init.shape[1]
     chains = n * restarts * 4
     if best_E is None:
@@ -163,9 +168,15 @@ def anneal(code, sched, seed, shot0, init, want_cfg=True, want_final=False, best
         final_E = final_E if final_E is not None else _empty((n, restarts, 4), torch.int32)
         final_cfg = final_cfg if final_cfg is not None else _empty((n, restarts, 4, 2 * code.words), torch.int32)
     assert best_E.numel() == chains
-    call("xzzx_anneal_warp" if per_warp else "xzzx_anneal", code.handle, sched.handle, seed, shot0, n, restarts,
-         _ptr(init), _ptr(best_E),
-         _ptr(best_cfg), _ptr(final_E), _ptr(final_cfg), _stream(stream))
+    if order != ORDER_COLOUR or emin != EMIN_PER_PHASE:
+        if per_warp:
+            raise ValueError("the warp-per-chain kernel runs the colour sweep with per-phase minima only")
+        call("xzzx_anneal_variant", code.handle, sched.handle, seed, shot0, n, restarts, int(order), int(emin),
+             _ptr(init), _ptr(best_E), _ptr(best_cfg), _ptr(final_E), _ptr(final_cfg), _stream(stream))
+    else:
+        call("xzzx_anneal_warp" if per_warp else "xzzx_anneal", code.handle, sched.handle, seed, shot0, n, restarts,
+             _ptr(init), _ptr(best_E),
+             _ptr(best_cfg), _ptr(final_E), _ptr(final_cfg), _stream(stream))
     return dict(best_E=best_E, best_cfg=best_cfg, final_E=final_E, final_cfg=final_cfg)
 
 

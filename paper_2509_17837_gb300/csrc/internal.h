@@ -28,8 +28,9 @@ xzzx_status cuda_fail(cudaError_t e, const char* what);
 // lattice row: 2 bits per qubit).
 constexpr int kMaxD = 31;
 
-// Philox purposes (top byte layout of the last counter word).
-constexpr uint32_t kTagNoise = 1, kTagGreedy = 2, kTagSA = 3;
+// Philox purposes (top byte layout of the last counter word).  kTagSite keys
+// the site and acceptance draws of the random-site Metropolis variant.
+constexpr uint32_t kTagNoise = 1, kTagGreedy = 2, kTagSA = 3, kTagSite = 4;
 
 // Sentinel index of the virtual boundary vertex in greedy pair keys.
 constexpr uint32_t kBoundary = 0xFFFFu;

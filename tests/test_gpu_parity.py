@@ -91,7 +91,8 @@ def test_greedy_parity_dense_random_syndromes(X, torch, d, density):
             assert np.array_equal(words_to_labels(init[s, i], d * d), ref)
 
 
-def anneal_case(X, torch, d, p, eta, n, R, kind, N, b0, b1, seed=3, shot0=11, scale=1024, per_warp=False):
+def anneal_case(X, torch, d, p, eta, n, R, kind, N, b0, b1, seed=3, shot0=11, scale=1024, per_warp=False,
+                order=0, emin=0):
     code = X.Code(d)
     noise = X.noise_from_eta(p, eta, 0, scale)
     pxyz = oracle_noise(noise)
@@ -100,7 +101,8 @@ def anneal_case(X, torch, d, p, eta, n, R, kind, N, b0, b1, seed=3, shot0=11, sc
     refs = np.array([[O.greedy(d, pxyz, scale, seed, shot0 + s, i, 1, osyn[s])[0] for i in range(R)]
                      for s in range(n)])
     init = gpu_words(torch, labels_to_words(refs))
-    out = X.anneal(code, sched, seed, shot0, init, want_cfg=True, want_final=True, per_warp=per_warp)
+    out = X.anneal(code, sched, seed, shot0, init, want_cfg=True, want_final=True, per_warp=per_warp, order=order,
+                   emin=emin)
     torch.cuda.synchronize()
     bE, fE = to_np(out["best_E"]), to_np(out["final_E"])
     bc = words_to_labels(to_np(out["best_cfg"]), d * d)
@@ -111,7 +113,11 @@ def anneal_case(X, torch, d, p, eta, n, R, kind, N, b0, b1, seed=3, shot0=11, sc
         for i in range(R):
             for P in range(4):
                 chain = ((shot0 + s) * R + i) * 4 + P
-                ref = O.anneal_chain(d, pxyz, scale, kind, N, b0, b1, seed, chain, refs[s, i] ^ Ls[P])
+                if order == 0 and emin == 0:
+                    ref = O.anneal_chain(d, pxyz, scale, kind, N, b0, b1, seed, chain, refs[s, i] ^ Ls[P])
+                else:
+                    ref = O.anneal_chain_variant(d, pxyz, scale, kind, N, b0, b1, seed, chain, refs[s, i] ^ Ls[P],
+                                                 order, emin)
                 assert bE[s, i, P] == ref["best_E"], (s, i, P)
                 assert fE[s, i, P] == ref["final_E"], (s, i, P)
                 assert np.array_equal(bc[s, i, P], ref["best"]), (s, i, P)
@@ -135,6 +141,53 @@ def test_anneal_warp_per_chain_parity(X, torch, d):
 def test_anneal_parity_schedules(X, torch, kind, N, b0, b1):
     anneal_case(X, torch, 7, 0.2, 100, 4, 3, kind, N, b0, b1)
     anneal_case(X, torch, 9, 0.2, 100, 2, 3, kind, N, b0, b1, per_warp=True)
+
+
+@pytest.mark.parametrize("d", [3, 5, 7, 11, 15, 17, 23, 31])
+@pytest.mark.parametrize("order,emin", [(1, 0), (1, 1), (0, 1)])
+def test_anneal_variant_parity(X, torch, d, order, emin):
+    """Random-site Metropolis and per-attempt minima (the literal Alg. 2 /
+    Alg. 3) equal the oracle's variants bit for bit."""
+    anneal_case(X, torch, d, 0.18, 30, 3, 5, X.LINEAR, 16 if d < 21 else 6, 0.1, 6.0, order=order, emin=emin)
+
+
+@pytest.mark.parametrize("order,emin", [(1, 1), (0, 1)])
+def test_anneal_variant_paper_schedule(X, torch, order, emin):
+    anneal_case(X, torch, 9, 0.12, 10, 2, 3, X.PAPER_LOG, 30, 0.9, 1.0, order=order, emin=emin, shot0=(1 << 31) + 3)
+
+
+def test_anneal_variant_colour_equals_main_kernel(X, torch):
+    """order 0 / emin 0 of the variant kernel is the main kernel's sweep: equal
+    outputs on a batch of several CTAs with a ragged tail; emin 1 follows the
+    same trajectory and never reports a higher minimum."""
+    from paper_2509_17837_gb300 import api
+    d, R, n = 11, 7, 37
+    code = X.Code(d)
+    noise = X.noise_from_eta(0.16, 100, 0, 1024)
+    sched = X.Schedule(noise, 50, 0.05, 20.0)
+    err, syn = X.sample_errors(code, noise, 5, 0, n)
+    init, _ = X.greedy_init(code, noise, 5, 0, syn, R)
+    a = X.anneal(code, sched, 5, 0, init, want_final=True)
+    b = {k: torch.empty_like(v) for k, v in a.items()}
+    api.call("xzzx_anneal_variant", code.handle, sched.handle, 5, 0, n, R, 0, 0, api._ptr(init), api._ptr(b["best_E"]),
+             api._ptr(b["best_cfg"]), api._ptr(b["final_E"]), api._ptr(b["final_cfg"]), api._stream(None))
+    v = X.anneal(code, sched, 5, 0, init, want_final=True, order=0, emin=1)
+    torch.cuda.synchronize()
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    assert bool((v["best_E"] <= a["best_E"]).all())
+    assert torch.equal(v["final_E"], a["final_E"]) and torch.equal(v["final_cfg"], a["final_cfg"])
+
+
+def test_anneal_variant_rejects_bad_modes(X, torch):
+    code = X.Code(5)
+    sched = X.Schedule(X.noise_from_eta(0.1, 1.0), 4, 0.1, 1.0)
+    init = torch.zeros((1, 1, 2 * code.words), dtype=torch.int32, device="cuda")
+    for order, emin in [(2, 0), (0, -1), (-1, 1)]:
+        with pytest.raises(X.XzzxError):
+            X.anneal(code, sched, 1, 0, init, order=order, emin=emin)
+    with pytest.raises(ValueError):
+        X.anneal(code, sched, 1, 0, init, order=1, per_warp=True)
 
 
 def test_anneal_parity_large_chain_ids(X, torch):

@@ -39,11 +39,10 @@ def _worker(rank, world, port, out_dir):
     pxyz = O.noise_from_eta(0.12, 1.0, O.PAPER_ETA)
     err, syn = O.sample(3, pxyz, 5, base, STEPS * S)
     out = O.decode(3, pxyz, 1024, O.LINEAR, 40, 0.1, 10.0, 5, base, 4, syn, err)
-    fails = torch.tensor([int(out["fail"].sum())], dtype=torch.int64)
-    dist.all_reduce(fails)
+    fails = bench.sum_over_ranks([float(out["fail"].sum())], dist, "cpu")
     slowest = bench.max_over_ranks([1.0 + rank, 5.0 - rank], dist, "cpu")
     np.save(os.path.join(out_dir, "rank%d.npy" % rank),
-            np.array([base, int(fails[0]), slowest[0], slowest[1]], dtype=np.float64))
+            np.array([base, fails[0], slowest[0], slowest[1]], dtype=np.float64))
     dist.destroy_process_group()
 
 
