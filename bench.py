@@ -385,12 +385,11 @@ def run_large(args):
         err, syn = X.sample_errors(code, noise, seed + i, 0, S * (args.steps + 1))
         cases.append((noise, sched, seed + i, err, syn))
     ws = torch.empty(X.decode_workspace_size(code, S, R), dtype=torch.uint8, device="cuda")
-    fails = 0
+    fails = [0] * len(cases)
 
     def step(k):
-        nonlocal fails
         ms = 0.0
-        for noise, sched, sd, err, syn in cases:
+        for ci, (noise, sched, sd, err, syn) in enumerate(cases):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             out = X.decode_batch(code, noise, sched, sd, k * S, syn[k * S:(k + 1) * S], R,
@@ -398,11 +397,11 @@ def run_large(args):
             e1.record(stream)
             e1.synchronize()
             ms += e0.elapsed_time(e1)
-            fails += int(out["fail"].sum())
+            fails[ci] += int(out["fail"].sum())
         return ms
 
     step(0)
-    fails = 0
+    fails = [0] * len(cases)
     ms = sum(step(k + 1) for k in range(args.steps)) / args.steps
     shots = S * len(LARGE_PS)
     att = shots * 4 * R * N * (d * d - 1) / (ms / 1e3)
@@ -415,11 +414,84 @@ def run_large(args):
         "data": "synthetic (library sampler, seeded)",
         "config": {"workload": "d=31 rotated XZZX, eta=1000, p in {0.15..0.30}, 256 restarts (1024 chains)/shot, "
                                "1e4 sweeps, linear beta 0.02->30, scale 4096", "shots_per_p_per_step": S},
-        "shots_per_s": shots / (ms / 1e3), "logical_failures": fails, "shots_timed": shots * args.steps,
-        "logical_error_rate_all_p": stats.ler_record(None, fails, shots * args.steps),
+        "shots_per_s": shots / (ms / 1e3), "shots_timed": shots * args.steps,
+        "logical_error_rates": [stats.ler_record(p, f, S * args.steps) for p, f in zip(LARGE_PS, fails)],
         "roofline": {"bound": "alu", "achieved": att * I_ALG / 1e12, "peak": peak, "unit": "Tinst/s",
                      "frac": att * I_ALG / 1e12 / peak, "traffic": None,
                      "peak_basis": "152 SMs x 128 lanes x 2070 MHz"}}))
+
+
+# --------------------------------------------------------------------------- logical error rate curves
+LER_D = (5, 7, 9)
+LER_GRID = {1.0: (0.12, 0.14, 0.16, 0.18, 0.20, 0.22, 0.24), 5.0: (0.14, 0.16, 0.18, 0.20, 0.22, 0.24, 0.26),
+            10.0: (0.06, 0.08, 0.10, 0.12, 0.14, 0.16, 0.18)}
+# finite-size threshold estimates the paper states for its own SA decoder (context only)
+LER_PAPER_PTH = {1.0: 0.18, 5.0: 0.2, 10.0: 0.11}
+
+
+def crossing(ps, lo_d, hi_d):
+    """p where LER(hi_d) - LER(lo_d) changes sign (linear interpolation), or None."""
+    diff = [h - l for l, h in zip(lo_d, hi_d)]
+    for k in range(len(ps) - 1):
+        if diff[k] < 0 <= diff[k + 1]:
+            return ps[k] + (ps[k + 1] - ps[k]) * (-diff[k]) / (diff[k + 1] - diff[k])
+    return None
+
+
+def run_ler(args):
+    """Logical error rate vs p for d = 5, 7, 9 under depolarizing, 1:5:1 and
+    1:10:1 Y-biased noise with the paper's decoder settings (N_beta = 100 log
+    schedule 0.9 -> 1.0 beta_N, N_SA = 100, randomised greedy references), for
+    the colour sweep and the literal random-site / per-attempt-minimum form."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2509_17837_gb300 as X
+    from paper_2509_17837_gb300 import stats
+    NSA, NB, shots, chunk = 100, 100, args.ler_shots, 25000
+    forms = {"colour": (X.ORDER_COLOUR, X.EMIN_PER_PHASE), "literal": (X.ORDER_RANDOM_SITE, X.EMIN_PER_ATTEMPT)}
+    curves, anneal_ms, attempts, total_shots = {}, {k: 0.0 for k in forms}, {k: 0 for k in forms}, 0
+    t_wall = time.perf_counter()
+    for eta, ps in LER_GRID.items():
+        for d in LER_D:
+            code = X.Code(d)
+            for pi, p in enumerate(ps):
+                noise = X.noise_from_eta(p, eta, X.CONVENTION_PAPER, 1024)
+                sched = X.Schedule(noise, NB, 0.9, 1.0, X.PAPER_LOG)
+                seed = 0x1E2 + 1000 * int(eta) + pi
+                for form, (order, emin) in forms.items():
+                    fails = 0
+                    for s0 in range(0, shots, chunk):
+                        n = min(chunk, shots - s0)
+                        err, syn = X.sample_errors(code, noise, seed, s0, n)
+                        init, cb = X.greedy_init(code, noise, seed, s0, syn, NSA)
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record()
+                        a = X.anneal(code, sched, seed, s0, init, want_cfg=False, order=order, emin=emin)
+                        e1.record()
+                        r = X.decode_reduce(code, init, cb, a["best_E"], true_errors=err)
+                        fails += int(r["fail"].sum())
+                        anneal_ms[form] += e0.elapsed_time(e1)
+                    attempts[form] += shots * NSA * 4 * NB * (d * d - 1)
+                    total_shots += shots
+                    curves.setdefault(form, {}).setdefault("%g" % eta, {}).setdefault(str(d), []).append(
+                        stats.ler_record(p, fails, shots))
+    wall = time.perf_counter() - t_wall
+    cross = {form: {e: {"d5_d7": crossing(LER_GRID[float(e)], [r["ler"] for r in c["5"]], [r["ler"] for r in c["7"]]),
+                        "d7_d9": crossing(LER_GRID[float(e)], [r["ler"] for r in c["7"]], [r["ler"] for r in c["9"]])}
+                    for e, c in fc.items()} for form, fc in curves.items()}
+    print(json.dumps({
+        "metric": "logical error rate vs p (d=5,7,9) with the paper's decoder settings",
+        "value": total_shots / wall, "unit": "decoded shots/s (whole sweep, wall clock)", "n_gpus": 1,
+        "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic (library sampler, seeded)",
+        "config": {"workload": "d in {5,7,9}, eta in {1,5,10} (px:py:pz = 1:eta:1), 7 values of p each, %d shots "
+                               "per point, N_SA=100, N_beta=100, log schedule 0.9->1.0 beta_N" % shots,
+                   "forms": {"colour": "colour sweep, minimum per colour phase",
+                             "literal": "random generator per attempt, minimum per attempt (Alg. 2 / Alg. 3)"}},
+        "anneal_attempts_per_s": {k: attempts[k] / (anneal_ms[k] / 1e3) for k in forms},
+        "curves": curves, "crossings": cross, "paper_threshold_estimates": LER_PAPER_PTH}))
 
 
 # --------------------------------------------------------------------------- our arm
@@ -434,7 +506,8 @@ def main():
     ap.add_argument("--cpu-shots", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="d11", choices=["d11", "uneven", "serve", "large"])
+    ap.add_argument("--workload", default="d11", choices=["d11", "uneven", "serve", "large", "ler"])
+    ap.add_argument("--ler-shots", type=int, default=100000)
     ap.add_argument("--large-shots-per-p", type=int, default=57)
     ap.add_argument("--uneven-shots", type=int, default=60000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
@@ -448,6 +521,8 @@ def main():
         return run_serve(args)
     if args.workload == "large" and args.impl == "ours":
         return run_large(args)
+    if args.workload == "ler" and args.impl == "ours":
+        return run_ler(args)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
