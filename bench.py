@@ -36,6 +36,10 @@ I_ALG = 30  # integer instructions per move attempt in the algorithmic count
 # capture of the current kernel (128,000 chains, 1.5373e6 B): each chain reads
 # its 32-byte reference (shared by its four cosets) and writes 4 bytes.
 ANNEAL_DRAM_BYTES_PER_CHAIN = 1.5373e6 / 128000
+# ALU-pipe lane instructions per attempt of anneal_kernel<11> (ncu
+# sm__inst_executed_pipe_alu of the same capture x 32 / attempts); the ALU
+# pipe takes 16 lanes per clock per SM sub-partition.
+ANNEAL_ALU_INST_PER_ATTEMPT = 15.3
 
 
 def workload_config(shots_per_p, world):
@@ -503,7 +507,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--shots-per-p", type=int, default=20000)
     ap.add_argument("--ref-shots", type=int, default=2)
-    ap.add_argument("--cpu-shots", type=int, default=12)
+    ap.add_argument("--cpu-shots", type=int, default=18)
+    ap.add_argument("--cpu-shots-per-core", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="d11", choices=["d11", "uneven", "serve", "large", "ler"])
@@ -656,7 +661,11 @@ def main():
                          "frac": achieved / peak, "traffic": ANNEAL_DRAM_BYTES_PER_CHAIN * S * RESTARTS * 4,
                          "kernel": "anneal_kernel<11>", "I_alg_per_attempt": I_ALG,
                          "peak_basis": "%d SMs x 4 SMSP x 32 lanes x %.0f MHz (median SM clock sampled in the timed region)"
-                                       % (n_sm, f_mhz)},
+                                       % (n_sm, f_mhz),
+                         "secondary_alu_pipe": {
+                             "alu_inst_per_attempt": ANNEAL_ALU_INST_PER_ATTEMPT,
+                             "peak_attempts_per_s": n_sm * 4 * 16 * f_mhz * 1e6 / ANNEAL_ALU_INST_PER_ATTEMPT,
+                             "frac": anneal_rate / (n_sm * 4 * 16 * f_mhz * 1e6 / ANNEAL_ALU_INST_PER_ATTEMPT)}},
             "clocks": clocks, "gpu_launches": 3 * len(PS) * args.steps,
             "logical_error_rates": [stats.ler_record(p, f, S * args.steps * world) for p, f in zip(PS, fail_dev)],
             "wall_s_timed_region": wall,
@@ -699,7 +708,7 @@ def main():
                                      "host syndromes/errors copied in, classes and failure flags copied out" % S}
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args.cpu_shots)
-        result["cpu_baseline_all_cores"] = cpu_baseline_all_cores(max(1, args.cpu_shots // 2))
+        result["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.cpu_shots_per_core)
     if rank == 0:
         print(json.dumps(result))
     if world > 1:
