@@ -8,6 +8,9 @@ import this package; the product path never does.
 Configurations are numpy ``uint8`` arrays with one two-bit Pauli per qubit
 (I=0, Z=1, X=2, Y=3); syndromes are ``uint8`` arrays with one bit per
 stabilizer in stabilizer-index order.
+
+Every function takes a code id: the distance d for the rotated layout, or
+``planar(d)`` for the paper's planar layout.
 """
 import ctypes as C
 import os
@@ -23,6 +26,20 @@ INIT_GREEDY, INIT_GREEDY_RANDOM, INIT_BOUNDARY = 0, 1, 2
 ORDER_COLOUR, ORDER_RANDOM_SITE = 0, 1
 EMIN_PER_PHASE, EMIN_PER_ATTEMPT = 0, 1
 BASELINE_ETA, PAPER_ETA = 0, 1
+PLANAR_ID = 1000
+
+
+def planar(d):
+    """Code id of the planar layout of distance d."""
+    return d + PLANAR_ID
+
+
+def distance(code_id):
+    return code_id % PLANAR_ID
+
+
+def _nq(d):
+    return code_sizes(d)[0]
 
 
 def lib():
@@ -93,7 +110,7 @@ def code_faces(d):
 
 
 def logicals(d):
-    nq = d * d
+    nq = _nq(d)
     LX, LZ = np.zeros(nq, np.uint8), np.zeros(nq, np.uint8)
     _check(lib().orc_logicals(d, _ptr(LX), _ptr(LZ)), "logicals")
     return LX, LZ
@@ -145,7 +162,7 @@ def boundary_distance(d, pxyz, scale):
 
 def greedy(d, pxyz, scale, seed, shot, restart, randomised, syn):
     syn = np.ascontiguousarray(syn, np.uint8)
-    R = np.zeros(d * d, np.uint8)
+    R = np.zeros(_nq(d), np.uint8)
     w = C.c_int64()
     _check(lib().orc_greedy(d, *pxyz, scale, seed, shot, restart, randomised, _ptr(syn), _ptr(R),
                             C.byref(w)), "greedy")
@@ -153,13 +170,13 @@ def greedy(d, pxyz, scale, seed, shot, restart, randomised, syn):
 
 
 def walk_internal(d, u, v):
-    R = np.zeros(d * d, np.uint8)
+    R = np.zeros(_nq(d), np.uint8)
     rc = lib().orc_walk_internal(d, u, v, _ptr(R))
     return (R if rc == 0 else None)
 
 
 def walk_boundary(d, pxyz, scale, u):
-    R = np.zeros(d * d, np.uint8)
+    R = np.zeros(_nq(d), np.uint8)
     rc = lib().orc_walk_boundary(d, *pxyz, scale, u, _ptr(R))
     return (R if rc == 0 else None)
 
@@ -174,7 +191,7 @@ def accept_threshold(beta, dE, scale):
 
 def anneal_chain(d, pxyz, scale, kind, n_sweeps, beta0, beta1, seed, chain, init, trace=False):
     init = np.ascontiguousarray(init, np.uint8)
-    nq = d * d
+    nq = _nq(d)
     best, fin = np.zeros(nq, np.uint8), np.zeros(nq, np.uint8)
     bE, fE = C.c_int32(), C.c_int32()
     tr = np.zeros(max(n_sweeps, 1), np.int32) if trace else None
@@ -190,7 +207,7 @@ def decode(d, pxyz, scale, kind, n_sweeps, beta0, beta1, seed, shot0, restarts, 
            randomised=1, want_chains=False):
     syn = np.ascontiguousarray(syn, np.uint8)
     n = syn.shape[0]
-    nq = d * d
+    nq = _nq(d)
     cls = np.zeros(n, np.uint8)
     E4 = np.zeros((n, 4), np.int32)
     rec = np.zeros((n, nq), np.uint8)
@@ -221,7 +238,7 @@ def bruteforce(d, pxyz, scale, R):
 
 def coset_energies(d, pxyz, scale, start):
     start = np.ascontiguousarray(start, np.uint8)
-    m = d * d - 1
+    m = code_sizes(d)[1]
     out = np.zeros(1 << m, np.int32)
     _check(lib().orc_coset_energies(d, *pxyz, scale, _ptr(start), _ptr(out)), "coset_energies")
     return out
@@ -230,7 +247,7 @@ def coset_energies(d, pxyz, scale, start):
 def anneal_chain_variant(d, pxyz, scale, kind, n_sweeps, beta0, beta1, seed, chain, init, order, emin,
                          trace=False):
     init = np.ascontiguousarray(init, np.uint8)
-    nq = d * d
+    nq = _nq(d)
     best, fin = np.zeros(nq, np.uint8), np.zeros(nq, np.uint8)
     bE, fE = C.c_int32(), C.c_int32()
     tr = np.zeros(max(n_sweeps, 1), np.int32) if trace else None

@@ -88,28 +88,55 @@ const uint32_t TAG_NOISE = 1, TAG_GREEDY = 2, TAG_SA = 3;
 // inside the lattice.  Faces: bulk a,b in [0,d-2]; top a=-1 with b odd;
 // bottom a=d-1 with b even; left b=-1 with a even; right b=d-1 with a odd.
 // ---------------------------------------------------------------------------
+//
+// The planar layout (the paper's own lattice, Sec. "The XZZX code"): sites
+// (r, c) of a (2d-1) x (2d-1) grid, data qubits where r+c is even
+// (d^2 + (d-1)^2 of them), faces where r+c is odd (2d(d-1)).  Face (i, j)
+// has corners left=(i,j-1), up=(i-1,j), down=(i+1,j), right=(i,j+1) and
+// G_f = X_left Z_up Z_down X_right (Eq. stabilizer_generator), truncated to
+// the three corners inside the grid on the boundary.  Qubit (r, c) has index
+// (r>>1)(2d-1) + (r odd ? d : 0) + (c>>1), i.e. row-major over the qubit sites.
+// ---------------------------------------------------------------------------
+const int LAYOUT_ROTATED = 0, LAYOUT_PLANAR = 1;
+
 struct Face {
-  int a, b;
-  int colour4;    // sweep colour (a&1)|((b&1)<<1), two's complement
-  int colour2;    // decoding-graph colour (a+b)&1
-  int corner[4];  // qubit index of TL,TR,BL,BR or -1 when outside
+  int a, b;       // rotated: face (a, b); planar: face site (i, j)
+  int colour4;    // sweep colour: four classes of pairwise disjoint generators
+  int colour2;    // decoding-graph colour
+  int ia, ib;     // coordinates of the face's SA draw inside its colour
+  int corner[4];  // qubit of the X, Z, Z, X corner (rotated TL,TR,BL,BR; planar left,up,down,right) or -1
 };
 
-const uint8_t CORNER_PAULI[4] = {PX, PZ, PZ, PX};  // TL,TR,BL,BR
+const uint8_t CORNER_PAULI[4] = {PX, PZ, PZ, PX};
 
 struct Code {
   int d = 0;
+  int layout = LAYOUT_ROTATED;
   int nq = 0;
-  std::vector<Face> faces;       // sorted by (colour4, a, b): the stabilizer index
-  std::vector<int> face_at;      // (a+1)*(d+1)+(b+1) -> index or -1
+  std::vector<Face> faces;       // sorted into the stabilizer index order
+  std::vector<int> face_at;      // face coordinates -> index or -1
   std::vector<uint8_t> LX, LZ;   // logical operators, one Pauli per qubit
   int colour_start[5];           // faces of colour c are [start[c], start[c+1])
 
   int face_index(int a, int b) const {
+    if (layout == LAYOUT_PLANAR) {
+      const int g = 2 * d - 1;
+      if (a < 0 || a >= g || b < 0 || b >= g) return -1;
+      return face_at[a * g + b];
+    }
     if (a < -1 || a > d - 1 || b < -1 || b > d - 1) return -1;
     return face_at[(a + 1) * (d + 1) + (b + 1)];
   }
-  bool qubit_in(int r, int c) const { return r >= 0 && r < d && c >= 0 && c < d; }
+  // Index of the data qubit at (r, c), or -1 when there is none.
+  int qubit(int r, int c) const {
+    if (layout == LAYOUT_PLANAR) {
+      const int g = 2 * d - 1;
+      if (r < 0 || r >= g || c < 0 || c >= g || ((r + c) & 1)) return -1;
+      return (r >> 1) * g + ((r & 1) ? d : 0) + (c >> 1);
+    }
+    return (r >= 0 && r < d && c >= 0 && c < d) ? r * d + c : -1;
+  }
+  bool qubit_in(int r, int c) const { return qubit(r, c) >= 0; }
 };
 
 bool face_present(int d, int a, int b) {
@@ -122,9 +149,12 @@ bool face_present(int d, int a, int b) {
   return false;
 }
 
+bool build_planar(int d, Code& code);
+
 bool build_code(int d, Code& code) {
   if (d < 3 || d % 2 == 0 || d > 255) return false;
   code.d = d;
+  code.layout = LAYOUT_ROTATED;
   code.nq = d * d;
   code.faces.clear();
   for (int a = -1; a <= d - 1; ++a) {
@@ -135,6 +165,8 @@ bool build_code(int d, Code& code) {
       f.b = b;
       f.colour4 = (a & 1) | ((b & 1) << 1);
       f.colour2 = (a + b) & 1;
+      f.ia = (a + 1) >> 1;
+      f.ib = (b + 1) >> 1;
       const int rr[4] = {a, a, a + 1, a + 1};
       const int cc[4] = {b, b + 1, b, b + 1};
       for (int k = 0; k < 4; ++k)
@@ -160,6 +192,56 @@ bool build_code(int d, Code& code) {
   code.LZ.assign(code.nq, PI_);
   for (int c = 0; c < d; ++c) code.LZ[0 * d + c] = (c % 2 == 0) ? PZ : PX;
   for (int r = 0; r < d; ++r) code.LX[r * d + 0] = (r % 2 == 0) ? PX : PZ;
+  return true;
+}
+
+// The planar layout.  Sweep colour of face (i, j): (i & 1) | (((i+j-1)/2 & 1) << 1);
+// two faces share a qubit only when they differ by (+-1, +-1), (+-2, 0) or
+// (0, +-2), and each of those changes the colour.  The decoding-graph colour
+// is i & 1 (faces on even rows meet the left and right boundaries, faces on odd
+// rows the top and bottom ones).  SA draw coordinates ia = i >> 1, ib = j >> 2
+// are distinct within a colour.  Stabilizer index order: (colour4, ib, ia), so
+// that the four faces sharing one draw block are consecutive.  L_Z = Z on the
+// qubits of row 0 (left to right); L_X = X on the qubits of column 0 (top to
+// bottom).
+bool build_planar(int d, Code& code) {
+  if (d < 3 || d % 2 == 0 || d > 127) return false;
+  const int g = 2 * d - 1;
+  code.d = d;
+  code.layout = LAYOUT_PLANAR;
+  code.nq = d * d + (d - 1) * (d - 1);
+  code.faces.clear();
+  for (int i = 0; i < g; ++i) {
+    for (int j = 0; j < g; ++j) {
+      if (((i + j) & 1) == 0) continue;
+      Face f;
+      f.a = i;
+      f.b = j;
+      f.colour4 = (i & 1) | ((((i + j - 1) >> 1) & 1) << 1);
+      f.colour2 = i & 1;
+      f.ia = i >> 1;
+      f.ib = j >> 2;
+      f.corner[0] = code.qubit(i, j - 1);
+      f.corner[1] = code.qubit(i - 1, j);
+      f.corner[2] = code.qubit(i + 1, j);
+      f.corner[3] = code.qubit(i, j + 1);
+      code.faces.push_back(f);
+    }
+  }
+  std::stable_sort(code.faces.begin(), code.faces.end(), [](const Face& x, const Face& y) {
+    if (x.colour4 != y.colour4) return x.colour4 < y.colour4;
+    if (x.ib != y.ib) return x.ib < y.ib;
+    return x.ia < y.ia;
+  });
+  code.face_at.assign(g * g, -1);
+  for (int k = 0; k < (int)code.faces.size(); ++k) code.face_at[code.faces[k].a * g + code.faces[k].b] = k;
+  for (int c = 0; c <= 4; ++c) code.colour_start[c] = 0;
+  for (const Face& f : code.faces) code.colour_start[f.colour4 + 1]++;
+  for (int c = 0; c < 4; ++c) code.colour_start[c + 1] += code.colour_start[c];
+  code.LX.assign(code.nq, PI_);
+  code.LZ.assign(code.nq, PI_);
+  for (int c = 0; c < g; c += 2) code.LZ[code.qubit(0, c)] = PZ;
+  for (int r = 0; r < g; r += 2) code.LX[code.qubit(r, 0)] = PX;
   return true;
 }
 
@@ -276,12 +358,51 @@ std::vector<uint8_t> sample_error(const Code& code, const Noise& n, uint64_t see
 
 // ---------------------------------------------------------------------------
 // Decoding graphs (Sec. "Principles of error detection and correction").
-// The Z component of qubit (r,c) is an edge between faces (r-1,c-1) and (r,c);
-// its X component an edge between faces (r-1,c) and (r,c-1).  A missing end
-// face makes the edge a boundary edge.  Z edges weigh Wt_z, X edges Wt_x
-// (Eqs. distance_u_v_internal, coeff_in_distance).
+// Rotated: the Z component of qubit (r,c) is an edge between faces (r-1,c-1)
+// and (r,c); its X component an edge between faces (r-1,c) and (r,c-1).
+// Planar: the Z component of qubit (r,c) is the horizontal edge between faces
+// (r,c-1) and (r,c+1), its X component the vertical edge between (r-1,c) and
+// (r+1,c).  A missing end face makes the edge a boundary edge.  Z edges weigh
+// Wt_z, X edges Wt_x (Eqs. distance_u_v_internal, coeff_in_distance).
 // ---------------------------------------------------------------------------
 const int BOUNDARY = 0xFFFF;
+
+// End faces (or -1) of the Z edge (e = 0) and the X edge (e = 1) of the qubit
+// at site (r, c).
+void qubit_edge_ends(const Code& code, int r, int c, int ends[2][2]) {
+  if (code.layout == LAYOUT_PLANAR) {
+    ends[0][0] = code.face_index(r, c - 1);
+    ends[0][1] = code.face_index(r, c + 1);
+    ends[1][0] = code.face_index(r - 1, c);
+    ends[1][1] = code.face_index(r + 1, c);
+    return;
+  }
+  ends[0][0] = code.face_index(r - 1, c - 1);
+  ends[0][1] = code.face_index(r, c);
+  ends[1][0] = code.face_index(r - 1, c);
+  ends[1][1] = code.face_index(r, c - 1);
+}
+
+// The four edges of a face in walking order: Z, Z, X, X.  Gives the face at
+// the other end (its coordinates) and the crossed qubit's site.  Rotated:
+// Z(+1,+1), Z(-1,-1), X(+1,-1), X(-1,+1), crossing qubit (max a, max b).
+// Planar: Z right, Z left (crossing (i, j+-1)), X down, X up (crossing (i+-1, j)).
+void face_step(const Code& code, int a, int b, int e, int& na, int& nb, int& qr, int& qc) {
+  if (code.layout == LAYOUT_PLANAR) {
+    const int di[4] = {0, 0, 1, -1}, dj[4] = {1, -1, 0, 0};
+    na = a + 2 * di[e];
+    nb = b + 2 * dj[e];
+    qr = a + di[e];
+    qc = b + dj[e];
+    return;
+  }
+  const int da[4] = {1, -1, 1, -1};
+  const int db[4] = {1, -1, -1, 1};
+  na = a + da[e];
+  nb = b + db[e];
+  qr = std::max(a, na);
+  qc = std::max(b, nb);
+}
 
 // Shortest distance from every face to the open boundary of its decoding
 // graph (the w(u,b) of Eq. distance_u_boundary).  Reading: the paper's closed
@@ -293,11 +414,12 @@ std::vector<int64_t> boundary_distance(const Code& code, const Noise& n) {
   // adjacency: (neighbour face or -1 for the boundary, weight)
   std::vector<std::vector<std::pair<int, int64_t>>> adj(nf);
   std::vector<int64_t> to_boundary(nf, INF);
-  const int d = code.d;
-  for (int r = 0; r < d; ++r) {
-    for (int c = 0; c < d; ++c) {
-      int ends[2][2] = {{code.face_index(r - 1, c - 1), code.face_index(r, c)},
-                        {code.face_index(r - 1, c), code.face_index(r, c - 1)}};
+  const int g = code.layout == LAYOUT_PLANAR ? 2 * code.d - 1 : code.d;
+  for (int r = 0; r < g; ++r) {
+    for (int c = 0; c < g; ++c) {
+      if (!code.qubit_in(r, c)) continue;
+      int ends[2][2];
+      qubit_edge_ends(code, r, c, ends);
       int64_t w[2] = {n.Wt_z, n.Wt_x};
       for (int e = 0; e < 2; ++e) {
         int f1 = ends[e][0], f2 = ends[e][1];
@@ -326,11 +448,14 @@ std::vector<int64_t> boundary_distance(const Code& code, const Noise& n) {
   return dist;
 }
 
-// Weighted Manhattan distance of Eq. distance_u_v_internal in rotated
-// coordinates: a Z step changes a+b by 2, an X step changes a-b by 2.
+// Weighted Manhattan distance of Eq. distance_u_v_internal.  Rotated
+// coordinates: a Z step changes a+b by 2, an X step changes a-b by 2.  Planar:
+// a Z step changes j by 2, an X step changes i by 2.
 int64_t internal_distance(const Code& code, const Noise& n, int u, int v) {
   const Face& fu = code.faces[u];
   const Face& fv = code.faces[v];
+  if (code.layout == LAYOUT_PLANAR)
+    return n.Wt_z * (std::llabs((int64_t)fu.b - fv.b) / 2) + n.Wt_x * (std::llabs((int64_t)fu.a - fv.a) / 2);
   int64_t ds = std::llabs((int64_t)(fu.a + fu.b) - (fv.a + fv.b)) / 2;
   int64_t dd = std::llabs((int64_t)(fu.a - fu.b) - (fv.a - fv.b)) / 2;
   return n.Wt_z * ds + n.Wt_x * dd;
@@ -343,7 +468,10 @@ void toggle(std::vector<uint8_t>& R, int q, bool z_step) { R[q] ^= z_step ? PZ :
 // (Alg. 5).  Reading: edges are added modulo two, and the minimal path is the
 // canonical walk that takes a Z step toward v whenever one is still needed and
 // both the next face and the crossed qubit exist, else an X step.
+bool walk_internal_planar(const Code& code, int u, int v, std::vector<uint8_t>& R);
+
 bool walk_internal(const Code& code, int u, int v, std::vector<uint8_t>& R) {
+  if (code.layout == LAYOUT_PLANAR) return walk_internal_planar(code, u, v, R);
   int a = code.faces[u].a, b = code.faces[u].b;
   const int ta = code.faces[v].a, tb = code.faces[v].b;
   int guard = 4 * code.d * code.d + 8;
@@ -379,33 +507,53 @@ bool walk_internal(const Code& code, int u, int v, std::vector<uint8_t>& R) {
   return true;
 }
 
+// Planar form of the same canonical walk: a horizontal Z step toward v while
+// the columns differ, then vertical X steps (every face between two faces of
+// one decoding-graph colour exists on the planar grid).
+bool walk_internal_planar(const Code& code, int u, int v, std::vector<uint8_t>& R) {
+  int i = code.faces[u].a, j = code.faces[u].b;
+  const int ti = code.faces[v].a, tj = code.faces[v].b;
+  if (((ti - i) & 1) || ((tj - j) & 1)) return false;
+  while (j != tj) {
+    const int s = tj > j ? 1 : -1;
+    if (code.face_index(i, j + 2 * s) < 0 || !code.qubit_in(i, j + s)) return false;
+    toggle(R, code.qubit(i, j + s), true);
+    j += 2 * s;
+  }
+  while (i != ti) {
+    const int s = ti > i ? 1 : -1;
+    if (code.face_index(i + 2 * s, j) < 0 || !code.qubit_in(i + s, j)) return false;
+    toggle(R, code.qubit(i + s, j), false);
+    i += 2 * s;
+  }
+  return true;
+}
+
 // Walk a face to its open boundary along a shortest path: at each face take
-// the first incident edge, in the order Z(+1,+1), Z(-1,-1), X(+1,-1), X(-1,+1),
-// that lowers the remaining boundary distance by exactly its own weight.
+// the first incident edge, in the walking order of face_step, that lowers the
+// remaining boundary distance by exactly its own weight.
 bool walk_to_boundary(const Code& code, const Noise& n, const std::vector<int64_t>& wb, int u,
                       std::vector<uint8_t>& R) {
-  const int da[4] = {1, -1, 1, -1};
-  const int db[4] = {1, -1, -1, 1};
   int cur = u;
-  int guard = 4 * code.d * code.d + 8;
+  int guard = 8 * code.d * code.d + 8;
   while (true) {
     if (--guard < 0) return false;
     int a = code.faces[cur].a, b = code.faces[cur].b;
     bool moved = false;
     for (int e = 0; e < 4 && !moved; ++e) {
       bool z_step = e < 2;
-      int na = a + da[e], nb = b + db[e];
-      int qr = std::max(a, na), qc = std::max(b, nb);
+      int na, nb, qr, qc;
+      face_step(code, a, b, e, na, nb, qr, qc);
       if (!code.qubit_in(qr, qc)) continue;
       int64_t w = z_step ? n.Wt_z : n.Wt_x;
       int nf = code.face_index(na, nb);
       if (nf < 0) {
         if (w == wb[cur]) {
-          toggle(R, qr * code.d + qc, z_step);
+          toggle(R, code.qubit(qr, qc), z_step);
           return true;
         }
       } else if (wb[nf] + w == wb[cur]) {
-        toggle(R, qr * code.d + qc, z_step);
+        toggle(R, code.qubit(qr, qc), z_step);
         cur = nf;
         moved = true;
       }
@@ -617,7 +765,7 @@ ChainResult anneal_chain_variant(const Code& code, const Noise& n, const Schedul
     }
     for (int colour = 0; colour < 4; ++colour) {
       for (int f = code.colour_start[colour]; f < code.colour_start[colour + 1]; ++f) {
-        const int ia = (code.faces[f].a + 1) >> 1, ib = (code.faces[f].b + 1) >> 1;
+        const int ia = code.faces[f].ia, ib = code.faces[f].ib;
         // dE = H(C G_f) - H(C), summed over the support of G_f.
         int64_t dE = 0;
         for (int k = 0; k < 4; ++k) {
@@ -717,7 +865,11 @@ bool decode_shot(const Code& code, const Noise& n, const Schedule& sch, uint64_t
   return true;
 }
 
-bool get_code(int d, Code& code) { return build_code(d, code); }
+// Code id: the distance d for the rotated layout, d + 1000 for the planar one.
+bool get_code(int id, Code& code) {
+  if (id >= 1000) return build_planar(id - 1000, code);
+  return build_code(id, code);
+}
 
 }  // namespace
 

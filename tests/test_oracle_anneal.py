@@ -30,7 +30,8 @@ def energy(W4, cfg):
     return int(np.asarray(W4, np.int64)[cfg].sum())
 
 
-@pytest.mark.parametrize("d,p,eta", [(3, 0.1, 10), (5, 0.15, 100), (11, 0.2, 100)])
+@pytest.mark.parametrize("d,p,eta", [(3, 0.1, 10), (5, 0.15, 100), (11, 0.2, 100), (O.planar(3), 0.1, 10),
+                                     (O.planar(7), 0.2, 100)])
 def test_chain_invariants(d, p, eta):
     pxyz = O.noise_from_eta(p, eta)
     W4, _ = O.make_noise(*pxyz, 1024)
@@ -53,7 +54,7 @@ def test_beta_zero_applies_every_generator():
     pxyz = O.noise_from_eta(0.1, 10)
     G = generators_from_syndromes(d)
     prod = np.bitwise_xor.reduce(G, axis=0)
-    init = np.zeros(d * d, np.uint8)
+    init = np.zeros(O.code_sizes(d)[0], np.uint8)
     one = O.anneal_chain(d, pxyz, 1024, O.LINEAR, 1, 0.0, 0.0, 3, 0, init)
     assert np.array_equal(one["final"], prod)
     two = O.anneal_chain(d, pxyz, 1024, O.LINEAR, 2, 0.0, 0.0, 3, 0, init)
@@ -71,9 +72,9 @@ def test_huge_beta_is_pure_descent():
         assert out["best_E"] == out["final_E"] == tr[-1]
 
 
-@pytest.mark.parametrize("p,eta,beta", [(0.25, 3, 0.15), (0.25, 3, 0.35), (0.3, 1.0, 1.0)])
-def test_detailed_balance_d3(p, eta, beta):
-    d = 3
+@pytest.mark.parametrize("d,p,eta,beta", [(3, 0.25, 3, 0.15), (3, 0.25, 3, 0.35), (3, 0.3, 1.0, 1.0),
+                                          (O.planar(3), 0.25, 3, 0.35), (O.planar(3), 0.3, 1.0, 1.0)])
+def test_detailed_balance_d3(d, p, eta, beta):
     pxyz = O.noise_from_eta(p, eta)
     W4, _ = O.make_noise(*pxyz, 1024)
     err, syn = O.sample(d, pxyz, 21, 3, 1)
@@ -165,7 +166,7 @@ def test_decode_outputs_consistent():
             assert m == E4[P]
 
 
-@pytest.mark.parametrize("d", [3, 5])
+@pytest.mark.parametrize("d", [3, 5, O.planar(3), O.planar(5)])
 def test_single_errors_are_corrected(d):
     pxyz = O.noise_from_eta(0.05, 1.0, O.PAPER_ETA)     # equal weights
     nq, ns, _ = O.code_sizes(d)
