@@ -17,13 +17,22 @@
  *   stream), validate every size on the host before launching anything, and
  *   run asynchronously on that stream.  A kernel fault surfaces as
  *   XZZX_ECUDA from the launch or from a later synchronising call.
- * - Rotated layout: data qubit (r, c), 0 <= r, c < d, has index q = r*d + c;
- *   the d*d - 1 generators are indexed colour by colour (colour =
+ * - Rotated layout (layout 0): data qubit (r, c), 0 <= r, c < d, has index
+ *   q = r*d + c; the d*d - 1 generators are indexed colour by colour (colour =
  *   (a&1) | ((b&1)<<1) of the face (a, b)), then by a, then by b.
- * - Configuration layout ("2w words"): w = ceil(d*d/32); words [0, w) hold the
- *   X bits, words [w, 2w) the Z bits; qubit q is bit (q & 31) of word q >> 5.
- *   Pauli I, X, Y, Z is (x, z) = (0,0), (1,0), (1,1), (0,1).
- * - Syndrome layout ("sw words"): sw = ceil((d*d-1)/32); generator f is bit
+ * - Planar layout (layout 1, the paper's lattice): the sites (r, c) of a
+ *   (2d-1) x (2d-1) grid; data qubits on the sites with r + c even
+ *   (n = d*d + (d-1)*(d-1)), indexed row-major over those sites
+ *   (q = (r>>1)(2d-1) + (r odd ? d : 0) + (c>>1)); faces on the sites with
+ *   r + c odd (2d(d-1) generators X_left Z_up Z_down X_right, three-body on
+ *   the boundary), indexed by colour = (i&1) | (((i+j-1)/2 & 1) << 1) of face
+ *   (i, j), then by j>>2, then by i>>1.  L_Z is Z on row 0, L_X is X on
+ *   column 0.
+ * - Configuration layout ("2w words"): w = ceil(n/32) for n data qubits;
+ *   words [0, w) hold the X bits, words [w, 2w) the Z bits; qubit q is bit
+ *   (q & 31) of word q >> 5.  Pauli I, X, Y, Z is (x, z) = (0,0), (1,0),
+ *   (1,1), (0,1).
+ * - Syndrome layout ("sw words"): sw = ceil(n_stab/32); generator f is bit
  *   (f & 31) of word f >> 5.
  * - Logical classes are indexed I=0, X=1, Y=2, Z=3.
  * - Randomness: Philox4x32-10 keyed by the 64-bit seed.  A draw depends only on
@@ -64,26 +73,31 @@ typedef struct xzzx_code xzzx_code;
 
 typedef struct {
   int32_t d;
-  int32_t n_qubits;        /* d*d */
-  int32_t n_stab;          /* d*d - 1 */
+  int32_t n_qubits;        /* rotated d*d; planar d*d + (d-1)*(d-1) */
+  int32_t n_stab;          /* n_qubits - 1 */
   int32_t words;           /* w: words per bit plane; a configuration is 2w words */
   int32_t syn_words;       /* sw: words per syndrome */
   int32_t colour_start[5]; /* generators of colour c are [start[c], start[c+1]) */
 } xzzx_code_info;
 
-/* Build the rotated distance-d XZZX code: G_f = X_TL Z_TR Z_BL X_BR on the
- * corners of face f inside the lattice (Eq. stabilizer_generator), L_Z along
- * row 0 and L_X along column 0.  d must be odd, 3 <= d <= 31.  layout 0 is the
- * rotated layout; any other value returns XZZX_EUNSUPPORTED.  Uploads the
- * tables to the current device.  *out is owned by the caller and released
- * with xzzx_free_code. */
+/* Build the distance-d XZZX code (Eq. stabilizer_generator).  layout 0: the
+ * rotated lattice, G_f = X_TL Z_TR Z_BL X_BR on the corners of face f inside
+ * the lattice, L_Z along row 0 and L_X along column 0.  layout 1: the paper's
+ * planar lattice (Sec. "The XZZX code"), G_f = X_left Z_up Z_down X_right.
+ * d must be odd, 3 <= d <= 31; another layout returns XZZX_EUNSUPPORTED.
+ * Planar codes run through sampling, greedy initialisation, xzzx_anneal,
+ * xzzx_anneal_variant, the decision and xzzx_decode_batch; the warp-per-chain
+ * kernel, batches and the server take rotated codes only (XZZX_EUNSUPPORTED).
+ * Uploads the tables to the current device.  *out is owned by the caller and
+ * released with xzzx_free_code. */
 xzzx_status xzzx_make_code(int d, int layout, xzzx_code** out);
 xzzx_status xzzx_get_code_info(const xzzx_code* code, xzzx_code_info* out);
 void xzzx_free_code(xzzx_code* code);
 
-/* Generator f as four corner qubits (TL, TR, BL, BR; -1 outside) and its face
- * coordinates; host arrays of n_stab entries (corners: 4*n_stab).  Any
- * pointer may be NULL. */
+/* Generator f as four corner qubits (-1 outside) in the order of its X, Z, Z,
+ * X factors (rotated TL, TR, BL, BR; planar left, up, down, right) and its
+ * face coordinates (rotated (a, b); planar (i, j)); host arrays of n_stab
+ * entries (corners: 4*n_stab).  Any pointer may be NULL. */
 xzzx_status xzzx_code_faces(const xzzx_code* code, int32_t* a, int32_t* b, int32_t* corners);
 
 /* ------------------------------------------------------------------------ */

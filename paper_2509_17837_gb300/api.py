@@ -15,6 +15,7 @@ from ._lib import (XZZX_ETIMEOUT, BatchCfg, BatchInfo, CodeInfo, Noise, Result, 
 
 LINEAR, PAPER_LOG = 0, 1
 CONVENTION_BASELINE, CONVENTION_PAPER = 0, 1
+LAYOUT_ROTATED, LAYOUT_PLANAR = 0, 1         # xzzx_make_code layouts
 ORDER_COLOUR, ORDER_RANDOM_SITE = 0, 1       # sweep order of xzzx_anneal_variant
 EMIN_PER_PHASE, EMIN_PER_ATTEMPT = 0, 1      # when the minimum is taken
 
@@ -39,15 +40,18 @@ def version():
 
 
 class Code:
-    """Rotated distance-d XZZX code (Sec. "The XZZX code"); tables on the current GPU."""
+    """Distance-d XZZX code (Sec. "The XZZX code"): the rotated lattice
+    (layout 0) or the paper's planar lattice (layout 1); tables on the current
+    GPU."""
 
-    def __init__(self, d, layout=0):
+    def __init__(self, d, layout=LAYOUT_ROTATED):
         h = C.c_void_p()
         call("xzzx_make_code", d, layout, C.byref(h))
         self._h = h
         info = CodeInfo()
         call("xzzx_get_code_info", h, C.byref(info))
         self.d = info.d
+        self.layout = layout
         self.n_qubits = info.n_qubits
         self.n_stab = info.n_stab
         self.words = info.words

@@ -65,9 +65,16 @@ xzzx_status launch_d(const AnnealArgs& A, cudaStream_t stream) {
 
 }  // namespace
 
+xzzx_status launch_anneal_planar(const xzzx_code* code, const xzzx_schedule* sched, uint64_t seed, uint64_t shot0,
+                                 int n_shots, int restarts, int order, int emin, const uint32_t* init, int32_t* best_E,
+                                 uint32_t* best_cfg, int32_t* final_E, uint32_t* final_cfg, cudaStream_t stream);
+
 xzzx_status launch_anneal(const xzzx_code* code, const xzzx_schedule* sched, uint64_t seed, uint64_t shot0,
                           int n_shots, int restarts, const uint32_t* init, int32_t* best_E, uint32_t* best_cfg,
                           int32_t* final_E, uint32_t* final_cfg, cudaStream_t stream) {
+  if (code->layout == kLayoutPlanar)  // colour sweep, minimum per colour phase
+    return launch_anneal_planar(code, sched, seed, shot0, n_shots, restarts, 0, 0, init, best_E, best_cfg, final_E,
+                                final_cfg, stream);
   AnnealArgs A;
   A.keys = philox_keys(seed);
   A.chain0 = shot0 * (uint64_t)restarts * 4u;

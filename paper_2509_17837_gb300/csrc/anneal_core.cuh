@@ -36,7 +36,7 @@
 namespace xzzx {
 namespace core {
 
-constexpr int kLutN = kSigTable;
+constexpr int kLutN = kSigRot;  // the rotated entries of the schedule's table
 
 template <int D>
 struct Shape {

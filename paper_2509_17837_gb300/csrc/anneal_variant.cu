@@ -263,6 +263,9 @@ __global__ void __launch_bounds__(kVarThreads) anneal_variant_kernel(const __gri
 }  // namespace
 
 xzzx_status check_anneal_args(const xzzx_code* code, const xzzx_schedule* sched, int n_shots, int restarts);
+xzzx_status launch_anneal_planar(const xzzx_code* code, const xzzx_schedule* sched, uint64_t seed, uint64_t shot0,
+                                 int n_shots, int restarts, int order, int emin, const uint32_t* init, int32_t* best_E,
+                                 uint32_t* best_cfg, int32_t* final_E, uint32_t* final_cfg, cudaStream_t stream);
 
 }  // namespace xzzx
 
@@ -278,6 +281,9 @@ extern "C" xzzx_status xzzx_anneal_variant(const xzzx_code* code, const xzzx_sch
   if (emin != 0 && emin != 1) return fail(XZZX_EINVAL, "emin must be 0 (per phase) or 1 (per attempt)");
   if (n_shots == 0) return XZZX_OK;
   if ((st = check_ptr(init, "init")) || (st = check_ptr(best_E, "best_E"))) return st;
+  if (code->layout == kLayoutPlanar)
+    return launch_anneal_planar(code, sched, seed, shot0, n_shots, restarts, order, emin, init, best_E, best_cfg,
+                                final_E, final_cfg, (cudaStream_t)stream);
   VariantArgs A;
   A.keys = philox_keys(seed);
   A.chain0 = shot0 * (uint64_t)restarts * 4u;

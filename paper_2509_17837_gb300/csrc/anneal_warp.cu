@@ -91,6 +91,7 @@ extern "C" xzzx_status xzzx_anneal_warp(const xzzx_code* code, const xzzx_schedu
                                         void* stream) {
   xzzx_status st = check_anneal_args(code, sched, n_shots, restarts);
   if (st) return st;
+  if (code->layout != kLayoutRotated) return fail(XZZX_EUNSUPPORTED, "the warp-per-chain kernel takes rotated codes");
   if (n_shots == 0) return XZZX_OK;
   if ((st = check_ptr(init, "init")) || (st = check_ptr(best_E, "best_E"))) return st;
   return launch_anneal_warp(code, sched, seed, shot0, n_shots, restarts, init, best_E, best_cfg, final_E, final_cfg,

@@ -150,6 +150,8 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
     const xzzx_segment& s = segs[i];
     xzzx_status st = check_code(s.code);
     if (st) return st;
+    if (s.code->layout != kLayoutRotated)
+      return fail(XZZX_EUNSUPPORTED, "segment " + std::to_string(i) + ": batches take rotated codes only");
     if (!s.noise || !s.sched) return fail(XZZX_EINVAL, "segment " + std::to_string(i) + ": noise or schedule is NULL");
     if (!s.sched->d_sig) return fail(XZZX_EINVAL, "segment schedule has no device tables");
     if (s.code->device != device || s.sched->device != device)

@@ -18,12 +18,13 @@ struct GreedyArgs {
   uint8_t* cbits;
 };
 
+template <class G>
 __global__ void __launch_bounds__(kWarps * 32) greedy_kernel(const __grid_constant__ GreedyArgs A) {
-  __shared__ Shared S;
+  __shared__ SharedT<G> S;
   const int k = blockIdx.x / A.groups;
-  greedy_cta(A.code, A.keys, A.shot0 + (uint64_t)k, blockIdx.x % A.groups, A.restarts, A.randomised, A.Wt_x, A.Wt_z,
-             A.syndromes + (size_t)k * A.code.sw, A.init + (size_t)k * A.restarts * 2 * A.code.w,
-             A.cbits + (size_t)k * A.restarts, S);
+  greedy_cta<G>(A.code, A.keys, A.shot0 + (uint64_t)k, blockIdx.x % A.groups, A.restarts, A.randomised, A.Wt_x,
+                A.Wt_z, A.syndromes + (size_t)k * A.code.sw, A.init + (size_t)k * A.restarts * 2 * A.code.w,
+                A.cbits + (size_t)k * A.restarts, S);
 }
 
 }  // namespace
@@ -46,7 +47,10 @@ xzzx_status launch_greedy(const xzzx_code* code, const xzzx_noise* noise, uint64
   A.cbits = cbits;
   const uint64_t grid = (uint64_t)n_shots * A.groups;
   if (grid > 0x7FFFFFFFull) return fail(XZZX_EINVAL, "too many shots x restarts for one launch");
-  greedy_kernel<<<(unsigned)grid, kWarps * 32, 0, stream>>>(A);
+  if (code->layout == kLayoutPlanar)
+    greedy_kernel<PlanarGeo><<<(unsigned)grid, kWarps * 32, 0, stream>>>(A);
+  else
+    greedy_kernel<RotGeo><<<(unsigned)grid, kWarps * 32, 0, stream>>>(A);
   XZZX_CUDA_TRY(cudaGetLastError());
   return XZZX_OK;
 }

@@ -31,102 +31,147 @@ constexpr int kWarps = 4;
 // Reference modes: greedy matching with lexicographic ties (Alg. 5), with
 // random ties (Alg. 6), or every defect joined to its nearer boundary.
 constexpr int kInitGreedy = 0, kInitGreedyRandom = 1, kInitBoundary = 2;
-constexpr int kMaxFaces = kMaxD * kMaxD - 1;
-constexpr int kMaxColour = kMaxFaces / 2;
-constexpr int kMaxAt = (kMaxD + 1) * (kMaxD + 1);
-constexpr int kMaxWords = (kMaxD * kMaxD + 31) / 32;
 constexpr int32_t kInf = 0x3FFFFFFF;
 
-
-struct Shared {
-  int16_t fa[kMaxFaces], fb[kMaxFaces];
-  int16_t at[kMaxAt];
-  int32_t wb[kMaxFaces];
-  int16_t defects[2][kMaxColour];
-  int n_def[2];
-  uint32_t syn[(kMaxFaces + 31) / 32];
-  int16_t best[kWarps][kMaxColour + 1];
-  int16_t partner[kWarps][kMaxColour + 1];
-  uint32_t cfg[kWarps][2 * kMaxWords];
-  int walk_error[kWarps];
+// Geometry of the rotated layout: faces (a, b), a, b in [-1, d-1]; qubit
+// (r, c) = r*d + c.  The four edges of a face in walking order: Z(+1,+1),
+// Z(-1,-1), X(+1,-1), X(-1,+1), crossing the qubit (max a, max b).
+struct RotGeo {
+  static constexpr int kMaxFaces = kMaxD * kMaxD - 1;
+  static constexpr int kMaxAt = (kMaxD + 1) * (kMaxD + 1);
+  static constexpr int kMaxWords = (kMaxD * kMaxD + 31) / 32;
+  __device__ static int at_size(int d) { return (d + 1) * (d + 1); }
+  __device__ static int face(const int16_t* at, int d, int a, int b) {
+    if (a < -1 || a > d - 1 || b < -1 || b > d - 1) return -1;
+    return at[(a + 1) * (d + 1) + (b + 1)];
+  }
+  __device__ static int qubit(int d, int r, int c) { return (r >= 0 && r < d && c >= 0 && c < d) ? r * d + c : -1; }
+  __device__ static void step(int a, int b, int e, int& na, int& nb, int& qr, int& qc) {
+    na = a + ((e & 1) ? -1 : 1);
+    nb = b + ((e == 1 || e == 2) ? -1 : 1);
+    qr = max(a, na);
+    qc = max(b, nb);
+  }
+  // Eq. distance_u_v_internal in rotated coordinates.
+  __device__ static int32_t w_int(int au, int bu, int av, int bv, int32_t Wt_x, int32_t Wt_z) {
+    return Wt_z * (abs((au + bu) - (av + bv)) >> 1) + Wt_x * (abs((au - bu) - (av - bv)) >> 1);
+  }
 };
 
-// The four edges of a face: crossed-qubit offset and step, Z edges first.
-__device__ __forceinline__ int step_a(int e) { return (e & 1) ? -1 : 1; }   // Z(+1,+1), Z(-1,-1), X(+1,-1), X(-1,+1)
-__device__ __forceinline__ int step_b(int e) { return (e == 1 || e == 2) ? -1 : 1; }
+// Geometry of the planar layout: faces (i, j), i + j odd, of the (2d-1)^2
+// grid; qubits on the sites with r + c even.  Edges in walking order: Z right
+// and Z left (crossing (i, j+-1)), X down and X up (crossing (i+-1, j)).
+struct PlanarGeo {
+  static constexpr int kMaxFaces = 2 * kMaxD * (kMaxD - 1);
+  static constexpr int kMaxAt = (2 * kMaxD - 1) * (2 * kMaxD - 1);
+  static constexpr int kMaxWords = (kMaxD * kMaxD + (kMaxD - 1) * (kMaxD - 1) + 31) / 32;
+  __device__ static int at_size(int d) { return (2 * d - 1) * (2 * d - 1); }
+  __device__ static int face(const int16_t* at, int d, int a, int b) {
+    const int g = 2 * d - 1;
+    if (a < 0 || a >= g || b < 0 || b >= g) return -1;
+    return at[a * g + b];
+  }
+  __device__ static int qubit(int d, int r, int c) {
+    const int g = 2 * d - 1;
+    if (r < 0 || r >= g || c < 0 || c >= g || ((r + c) & 1)) return -1;
+    return planar_qubit(d, r, c);
+  }
+  __device__ static void step(int a, int b, int e, int& na, int& nb, int& qr, int& qc) {
+    const int di = e < 2 ? 0 : (e == 2 ? 1 : -1);
+    const int dj = e < 2 ? (e == 0 ? 1 : -1) : 0;
+    na = a + 2 * di;
+    nb = b + 2 * dj;
+    qr = a + di;
+    qc = b + dj;
+  }
+  // Eq. distance_u_v_internal: a Z step moves j by 2, an X step moves i by 2.
+  __device__ static int32_t w_int(int au, int bu, int av, int bv, int32_t Wt_x, int32_t Wt_z) {
+    return Wt_z * (abs(bu - bv) >> 1) + Wt_x * (abs(au - av) >> 1);
+  }
+};
 
+template <class G>
+struct SharedT {
+  int16_t fa[G::kMaxFaces], fb[G::kMaxFaces];
+  int16_t at[G::kMaxAt];
+  int32_t wb[G::kMaxFaces];
+  int16_t defects[2][G::kMaxFaces / 2];
+  int n_def[2];
+  uint32_t syn[(G::kMaxFaces + 31) / 32];
+  int16_t best[kWarps][G::kMaxFaces / 2 + 1];
+  int16_t partner[kWarps][G::kMaxFaces / 2 + 1];
+  uint32_t cfg[kWarps][2 * G::kMaxWords];
+  int walk_error[kWarps];
+};
+using Shared = SharedT<RotGeo>;
+
+template <class G>
 struct Ctx {
-  const Shared& S;
+  const SharedT<G>& S;
   int d, w;
   int32_t Wt_x, Wt_z;
-  __device__ int face(int a, int b) const {
-    if (a < -1 || a > d - 1 || b < -1 || b > d - 1) return -1;
-    return S.at[(a + 1) * (d + 1) + (b + 1)];
-  }
-  __device__ bool qubit_in(int r, int c) const { return r >= 0 && r < d && c >= 0 && c < d; }
-  // Eq. distance_u_v_internal in rotated coordinates.
-  __device__ int32_t w_int(int u, int v) const {
-    const int su = S.fa[u] + S.fb[u], sv = S.fa[v] + S.fb[v];
-    const int du = S.fa[u] - S.fb[u], dv = S.fa[v] - S.fb[v];
-    return Wt_z * (abs(su - sv) >> 1) + Wt_x * (abs(du - dv) >> 1);
-  }
+  __device__ int face(int a, int b) const { return G::face(S.at, d, a, b); }
+  __device__ int qubit(int r, int c) const { return G::qubit(d, r, c); }
+  __device__ int32_t w_int(int u, int v) const { return G::w_int(S.fa[u], S.fb[u], S.fa[v], S.fb[v], Wt_x, Wt_z); }
 };
 
 __device__ __forceinline__ void toggle(uint32_t* cfg, int w, int q, bool z_step) {
   atomicXor(&cfg[(z_step ? w : 0) + (q >> 5)], 1u << (q & 31));
 }
 
-static __device__ bool walk_internal(const Ctx& X, int u, int v, uint32_t* cfg) {
+// Canonical internal walk: a Z step toward v whenever one is still needed and
+// both the next face and the crossed qubit exist, else an X step.
+template <class G>
+__device__ bool walk_internal(const Ctx<G>& X, int u, int v, uint32_t* cfg) {
   int a = X.S.fa[u], b = X.S.fb[u];
   const int ta = X.S.fa[v], tb = X.S.fb[v];
-  for (int guard = 0; guard < 4 * X.d * X.d + 8; ++guard) {
+  for (int guard = 0; guard < 8 * X.d * X.d + 8; ++guard) {
     if (a == ta && b == tb) return true;
-    const int ds = (ta + tb) - (a + b), dd = (ta - tb) - (a - b);
-    if (ds != 0) {
-      const int s = ds > 0 ? 1 : -1;
-      const int na = a + s, nb = b + s, qr = max(a, na), qc = max(b, nb);
-      if (X.face(na, nb) >= 0 && X.qubit_in(qr, qc)) {
-        toggle(cfg, X.w, qr * X.d + qc, true);
-        a = na;
-        b = nb;
-        continue;
-      }
+    bool moved = false;
+    for (int e = 0; e < 4 && !moved; ++e) {
+      int na, nb, qr, qc;
+      G::step(a, b, e, na, nb, qr, qc);
+      const bool z_step = e < 2;
+      // the step must lower the remaining distance of its own kind
+      const int32_t before = G::w_int(a, b, ta, tb, z_step ? 0 : 1, z_step ? 1 : 0);
+      const int32_t after = G::w_int(na, nb, ta, tb, z_step ? 0 : 1, z_step ? 1 : 0);
+      if (after != before - 1) continue;
+      const int q = X.qubit(qr, qc);
+      if (X.face(na, nb) < 0 || q < 0) continue;
+      toggle(cfg, X.w, q, z_step);
+      a = na;
+      b = nb;
+      moved = true;
     }
-    if (dd != 0) {
-      const int s = dd > 0 ? 1 : -1;
-      const int na = a + s, nb = b - s, qr = max(a, na), qc = max(b, nb);
-      if (X.face(na, nb) >= 0 && X.qubit_in(qr, qc)) {
-        toggle(cfg, X.w, qr * X.d + qc, false);
-        a = na;
-        b = nb;
-        continue;
-      }
-    }
-    return false;
+    if (!moved) return false;
   }
   return false;
 }
 
-static __device__ bool walk_boundary(const Ctx& X, int u, uint32_t* cfg) {
+// Walk to the open boundary: at each face the first edge, in walking order,
+// that lowers the boundary distance by exactly its own weight.
+template <class G>
+__device__ bool walk_boundary(const Ctx<G>& X, int u, uint32_t* cfg) {
   int cur = u;
-  for (int guard = 0; guard < 4 * X.d * X.d + 8; ++guard) {
+  for (int guard = 0; guard < 8 * X.d * X.d + 8; ++guard) {
     const int a = X.S.fa[cur], b = X.S.fb[cur];
     const int32_t here = X.S.wb[cur];
     bool moved = false;
     for (int e = 0; e < 4; ++e) {
-      const int na = a + step_a(e), nb = b + step_b(e);
-      const int qr = max(a, na), qc = max(b, nb);
-      if (!X.qubit_in(qr, qc)) continue;
+      int na, nb, qr, qc;
+      G::step(a, b, e, na, nb, qr, qc);
+      const int q = X.qubit(qr, qc);
+      if (q < 0) continue;
       const bool z_step = e < 2;
       const int32_t w = z_step ? X.Wt_z : X.Wt_x;
       const int nf = X.face(na, nb);
       if (nf < 0) {
         if (w == here) {
-          toggle(cfg, X.w, qr * X.d + qc, z_step);
+          toggle(cfg, X.w, q, z_step);
           return true;
         }
       } else if (X.S.wb[nf] + w == here) {
-        toggle(cfg, X.w, qr * X.d + qc, z_step);
+        toggle(cfg, X.w, q, z_step);
         cur = nf;
         moved = true;
         break;
@@ -140,9 +185,10 @@ static __device__ bool walk_boundary(const Ctx& X, int u, uint32_t* cfg) {
 // One CTA: references of restarts [group*kWarps, group*kWarps + kWarps)
 // of one shot.  syn: the shot's syndrome words; init / cbits: the shot's rows
 // (restarts x 2w words, restarts bytes).
+template <class G>
 __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K, uint64_t shot, int group, int restarts,
                                            int mode, int32_t Wt_x, int32_t Wt_z, const uint32_t* __restrict__ syn,
-                                           uint32_t* __restrict__ init, uint8_t* __restrict__ cbits, Shared& S) {
+                                           uint32_t* __restrict__ init, uint8_t* __restrict__ cbits, SharedT<G>& S) {
   const int d = C.d, ns = C.ns, w = C.w;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int i = group * kWarps + warp;
@@ -151,18 +197,19 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
     S.fa[f] = C.face_a[f];
     S.fb[f] = C.face_b[f];
   }
-  for (int j = tid; j < (d + 1) * (d + 1); j += blockDim.x) S.at[j] = C.face_at[j];
+  for (int j = tid; j < G::at_size(d); j += blockDim.x) S.at[j] = C.face_at[j];
   for (int j = tid; j < C.sw; j += blockDim.x) S.syn[j] = syn[j];
   __syncthreads();
-  Ctx X{S, d, w, Wt_x, Wt_z};
+  Ctx<G> X{S, d, w, Wt_x, Wt_z};
 
   // Boundary distances: start from the boundary edges, relax until stable.
   for (int f = tid; f < ns; f += blockDim.x) {
     const int a = S.fa[f], b = S.fb[f];
     int32_t best = kInf;
     for (int e = 0; e < 4; ++e) {
-      const int na = a + step_a(e), nb = b + step_b(e);
-      if (!X.qubit_in(max(a, na), max(b, nb)) || X.face(na, nb) >= 0) continue;
+      int na, nb, qr, qc;
+      G::step(a, b, e, na, nb, qr, qc);
+      if (X.qubit(qr, qc) < 0 || X.face(na, nb) >= 0) continue;
       best = min(best, e < 2 ? Wt_z : Wt_x);
     }
     S.wb[f] = best;
@@ -174,8 +221,9 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
       const int a = S.fa[f], b = S.fb[f];
       int32_t cur = S.wb[f];
       for (int e = 0; e < 4; ++e) {
-        const int na = a + step_a(e), nb = b + step_b(e);
-        if (!X.qubit_in(max(a, na), max(b, nb))) continue;
+        int na, nb, qr, qc;
+        G::step(a, b, e, na, nb, qr, qc);
+        if (X.qubit(qr, qc) < 0) continue;
         const int nf = X.face(na, nb);
         if (nf < 0) continue;
         const int32_t cand = S.wb[nf] + (e < 2 ? Wt_z : Wt_x);

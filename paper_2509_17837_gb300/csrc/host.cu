@@ -114,18 +114,80 @@ const char* xzzx_last_error(void) { return g_last_error.c_str(); }
 
 const char* xzzx_version(void) { return "xzzx-gb300 0.1 (sm_103a)"; }
 
+namespace xzzx {
+namespace {
+
+// The planar layout: faces (i, j), i + j odd, of the (2d-1)^2 grid, indexed in
+// the order (colour, j>>2, i>>1) with colour = (i&1) | (((i+j-1)/2 & 1) << 1);
+// corners left, up, down, right; L_Z = Z on row 0, L_X = X on column 0.
+void build_planar(xzzx_code* c) {
+  const int d = c->d, g = 2 * d - 1;
+  c->nq = d * d + (d - 1) * (d - 1);
+  c->w = (c->nq + 31) / 32;
+  c->face_at.assign((size_t)g * g, -1);
+  struct F {
+    int colour, ib, ia, i, j;
+  };
+  std::vector<F> fs;
+  for (int i = 0; i < g; ++i)
+    for (int j = 0; j < g; ++j)
+      if ((i + j) & 1) fs.push_back({(i & 1) | ((((i + j - 1) >> 1) & 1) << 1), j >> 2, i >> 1, i, j});
+  std::sort(fs.begin(), fs.end(), [](const F& x, const F& y) {
+    if (x.colour != y.colour) return x.colour < y.colour;
+    if (x.ib != y.ib) return x.ib < y.ib;
+    return x.ia < y.ia;
+  });
+  for (int k = 0; k < 5; ++k) c->colour_start[k] = 0;
+  auto site = [&](int r, int col) {
+    return (r >= 0 && r < g && col >= 0 && col < g) ? planar_qubit(d, r, col) : -1;
+  };
+  for (const F& f : fs) {
+    c->face_at[(size_t)f.i * g + f.j] = (int16_t)c->a.size();
+    c->a.push_back((int16_t)f.i);
+    c->b.push_back((int16_t)f.j);
+    c->c2.push_back((uint8_t)(f.i & 1));
+    c->c4.push_back((uint8_t)f.colour);
+    c->colour_start[f.colour + 1]++;
+    c->corners.push_back(site(f.i, f.j - 1));
+    c->corners.push_back(site(f.i - 1, f.j));
+    c->corners.push_back(site(f.i + 1, f.j));
+    c->corners.push_back(site(f.i, f.j + 1));
+  }
+  for (int k = 0; k < 4; ++k) c->colour_start[k + 1] += c->colour_start[k];
+  c->ns = (int)c->a.size();
+  c->sw = (c->ns + 31) / 32;
+  const int w = c->w;
+  c->logical.assign(4 * w, 0u);
+  uint32_t* LX = c->logical.data();
+  uint32_t* LZ = c->logical.data() + 2 * w;
+  for (int col = 0; col < g; col += 2) {
+    const int q = planar_qubit(d, 0, col);
+    LZ[w + (q >> 5)] |= 1u << (q & 31);  // Z
+  }
+  for (int r = 0; r < g; r += 2) {
+    const int q = planar_qubit(d, r, 0);
+    LX[q >> 5] |= 1u << (q & 31);  // X
+  }
+}
+
+}  // namespace
+}  // namespace xzzx
+
 xzzx_status xzzx_make_code(int d, int layout, xzzx_code** out) {
   if (!out) return fail(XZZX_EINVAL, "out is NULL");
   *out = nullptr;
-  if (layout != 0) return fail(XZZX_EUNSUPPORTED, "only the rotated layout (0) is built");
+  if (layout != kLayoutRotated && layout != kLayoutPlanar)
+    return fail(XZZX_EUNSUPPORTED, "layout must be 0 (rotated) or 1 (planar)");
   if (d < 3 || d > kMaxD || (d & 1) == 0) return fail(XZZX_EINVAL, "d must be odd and in [3, 31]");
   xzzx_code* c = new (std::nothrow) xzzx_code();
   if (!c) return fail(XZZX_ENOMEM, "host allocation");
   c->d = d;
-  c->nq = d * d;
+  c->layout = layout;
+  if (layout == kLayoutPlanar) build_planar(c);
+  c->nq = layout == kLayoutPlanar ? c->nq : d * d;
   c->w = (c->nq + 31) / 32;
-  c->face_at.assign((d + 1) * (d + 1), -1);
-  for (int colour = 0; colour < 4; ++colour) {
+  if (layout == kLayoutRotated) c->face_at.assign((d + 1) * (d + 1), -1);
+  for (int colour = 0; colour < 4 && layout == kLayoutRotated; ++colour) {
     c->colour_start[colour] = (int)c->a.size();
     const int pa = colour & 1, pb = colour >> 1;
     for (int a = -1; a <= d - 1; ++a) {
@@ -145,21 +207,23 @@ xzzx_status xzzx_make_code(int d, int layout, xzzx_code** out) {
       }
     }
   }
-  c->colour_start[4] = (int)c->a.size();
-  c->ns = (int)c->a.size();
-  c->sw = (c->ns + 31) / 32;
-  // L_X: column 0 alternating X, Z; L_Z: row 0 alternating Z, X.
-  const int w = c->w;
-  c->logical.assign(4 * w, 0u);
-  uint32_t* LX = c->logical.data();
-  uint32_t* LZ = c->logical.data() + 2 * w;
-  for (int r = 0; r < d; ++r) {
-    const int q = r * d;
-    (r % 2 == 0 ? LX : LX + w)[q >> 5] |= 1u << (q & 31);
-  }
-  for (int col = 0; col < d; ++col) {
-    const int q = col;
-    (col % 2 == 0 ? LZ + w : LZ)[q >> 5] |= 1u << (q & 31);
+  if (layout == kLayoutRotated) {
+    c->colour_start[4] = (int)c->a.size();
+    c->ns = (int)c->a.size();
+    c->sw = (c->ns + 31) / 32;
+    // L_X: column 0 alternating X, Z; L_Z: row 0 alternating Z, X.
+    const int w = c->w;
+    c->logical.assign(4 * w, 0u);
+    uint32_t* LX = c->logical.data();
+    uint32_t* LZ = c->logical.data() + 2 * w;
+    for (int r = 0; r < d; ++r) {
+      const int q = r * d;
+      (r % 2 == 0 ? LX : LX + w)[q >> 5] |= 1u << (q & 31);
+    }
+    for (int col = 0; col < d; ++col) {
+      const int q = col;
+      (col % 2 == 0 ? LZ + w : LZ)[q >> 5] |= 1u << (q & 31);
+    }
   }
   // Upload the device tables in one block.
   const size_t o_a = 0;
@@ -193,6 +257,7 @@ xzzx_status xzzx_make_code(int d, int layout, xzzx_code** out) {
   char* base = (char*)c->dev_block;
   DevCode& dv = c->dev;
   dv.d = d;
+  dv.layout = layout;
   dv.nq = c->nq;
   dv.ns = c->ns;
   dv.w = c->w;
@@ -288,28 +353,32 @@ xzzx_status xzzx_make_schedule(const xzzx_noise* noise, int kind, int n_sweeps, 
   s->beta0 = beta0;
   s->beta1 = beta1;
   s->noise = *noise;
-  // Energy change of each generator shape for each corner signature (compact
-  // table: bulk by its 8-bit signature TL|TR<<2|BL<<4|BR<<6, weight-2 shapes
-  // by their two present corners): X flips the x bit of TL and BR, Z flips
-  // the z bit of TR and BL.
-  const int flip[4] = {2, 1, 1, 2};
+  // Energy change of each generator shape for each corner signature.  Rotated
+  // (compact table: bulk by its 8-bit signature TL|TR<<2|BL<<4|BR<<6, weight-2
+  // shapes by their two present corners): X flips the x bit of TL and BR, Z
+  // flips the z bit of TR and BL.  Planar (bulk left|right<<2|up<<4|down<<6,
+  // three-body shapes by their present corners): X on left and right, Z on up
+  // and down.
   s->sig_dE.assign(kSigTable, 0);
   s->sig_class.assign(kSigTable, -1);
   std::set<int32_t> positive;
-  for (int y = 0; y < kNumTypes; ++y) {
+  auto fill = [&](int base, int mask, const int* flip) {
     int present[4], np = 0;
     for (int k = 0; k < 4; ++k)
-      if ((kCornerMask[y] >> k) & 1) present[np++] = k;
+      if ((mask >> k) & 1) present[np++] = k;
     for (int code = 0; code < (1 << (2 * np)); ++code) {
       int64_t dE = 0;
       for (int j = 0; j < np; ++j) {
         const int lab = (code >> (2 * j)) & 3;
         dE += (int64_t)noise->W[lab ^ flip[present[j]]] - (int64_t)noise->W[lab];
       }
-      s->sig_dE[sig_base(y) + code] = (int32_t)dE;
+      s->sig_dE[base + code] = (int32_t)dE;
       if (dE > 0) positive.insert((int32_t)dE);
     }
-  }
+  };
+  const int flip_rot[4] = {2, 1, 1, 2}, flip_planar[4] = {2, 2, 1, 1};
+  for (int y = 0; y < kNumTypes; ++y) fill(sig_base(y), kCornerMask[y], flip_rot);
+  for (int y = 0; y < kNumPShapes; ++y) fill(planar_sig_base(y), kPlanarCornerMask[y], flip_planar);
   s->dE_class.assign(positive.begin(), positive.end());
   s->n_classes = (int)s->dE_class.size();
   for (int i = 0; i < kSigTable; ++i) {

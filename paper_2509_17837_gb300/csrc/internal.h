@@ -35,15 +35,33 @@ constexpr uint32_t kTagNoise = 1, kTagGreedy = 2, kTagSA = 3, kTagSite = 4;
 // Sentinel index of the virtual boundary vertex in greedy pair keys.
 constexpr uint32_t kBoundary = 0xFFFFu;
 
-// Generator shapes: the bulk weight-4 face and the four weight-2 boundary
-// faces, by which corners exist.  Signature bits: TL 0-1, TR 2-3, BL 4-5, BR 6-7.
+// Code layouts: the rotated d x d lattice and the paper's planar lattice
+// (qubits on the sites (r, c), r + c even, of a (2d-1) x (2d-1) grid).
+constexpr int kLayoutRotated = 0, kLayoutPlanar = 1;
+
+// Rotated generator shapes: the bulk weight-4 face and the four weight-2
+// boundary faces, by which corners exist.  Signature bits: TL 0-1, TR 2-3,
+// BL 4-5, BR 6-7.
 enum FaceType { kBulk = 0, kTop = 1, kBottom = 2, kLeft = 3, kRight = 4, kNumTypes = 5 };
 constexpr int kCornerMask[kNumTypes] = {0xF, 0xC, 0x3, 0xA, 0x5};  // bit k = corner k present
-// Compact signature table: the 256 bulk signatures, then 16 entries per
-// weight-2 shape indexed by its two present corners (the first present corner
-// in bits 0-1, the second in bits 2-3).
-constexpr int kSigTable = 256 + 4 * 16;
+// Compact signature table of the rotated shapes: the 256 bulk signatures, then
+// 16 entries per weight-2 shape indexed by its two present corners (the first
+// present corner in bits 0-1, the second in bits 2-3).
+constexpr int kSigRot = 256 + 4 * 16;
 __host__ __device__ constexpr int sig_base(int type) { return type == kBulk ? 0 : 256 + 16 * (type - 1); }
+
+// Planar generator shapes.  Corner order left, right, up, down (Paulis X, X,
+// Z, Z); the bulk signature is left | right<<2 | up<<4 | down<<6, a
+// three-body shape's signature its three present corners in that order.
+enum PlanarShape { kPBulk = 0, kPNoUp = 1, kPNoDown = 2, kPNoLeft = 3, kPNoRight = 4, kNumPShapes = 5 };
+constexpr int kPlanarCornerMask[kNumPShapes] = {0xF, 0xB, 0x7, 0xE, 0xD};
+constexpr int kSigPlanar = 256 + 4 * 64;
+__host__ __device__ constexpr int planar_sig_base(int shape) {
+  return kSigRot + (shape == kPBulk ? 0 : 256 + 64 * (shape - 1));
+}
+// The schedule's (dE, class) table holds both: rotated entries [0, kSigRot),
+// planar entries [kSigRot, kSigTable).
+constexpr int kSigTable = kSigRot + kSigPlanar;
 
 // Round keys of Philox4x32-10 for one seed, in kernel-parameter space.
 struct PhiloxKeys {
@@ -54,18 +72,26 @@ PhiloxKeys philox_keys(uint64_t seed);
 // Device view of a code (pointers into the tables owned by xzzx_code).
 struct DevCode {
   int d, nq, ns, w, sw;
+  int layout;                // kLayoutRotated or kLayoutPlanar
   int colour_start[5];
-  const int16_t* face_a;     // ns
-  const int16_t* face_b;     // ns
-  const uint8_t* face_c2;    // ns, decoding-graph colour (a+b)&1
-  const int16_t* face_at;    // (d+1)^2, index of face (a,b) at (a+1)*(d+1)+(b+1), or -1
-  const uint32_t* logical;   // 2 x 2w words: L_X then L_Z, planar
+  const int16_t* face_a;     // ns (planar: row i of the face site)
+  const int16_t* face_b;     // ns (planar: column j)
+  const uint8_t* face_c2;    // ns, decoding-graph colour
+  const int16_t* face_at;    // rotated (d+1)^2 at (a+1)*(d+1)+(b+1); planar (2d-1)^2 at i*(2d-1)+j; -1 = none
+  const uint32_t* logical;   // 2 x 2w words: L_X then L_Z, bit planes
 };
+
+// Planar qubit index of site (r, c), r + c even, inside the (2d-1)^2 grid:
+// row-major over the qubit sites.
+__host__ __device__ inline int planar_qubit(int d, int r, int c) {
+  return (r >> 1) * (2 * d - 1) + ((r & 1) ? d : 0) + (c >> 1);
+}
 
 }  // namespace xzzx
 
 struct xzzx_code {
   int d = 0, nq = 0, ns = 0, w = 0, sw = 0;
+  int layout = 0;
   int colour_start[5] = {0, 0, 0, 0, 0};
   int device = -1;
   std::vector<int16_t> a, b;

@@ -12,6 +12,7 @@ namespace xzzx {
 namespace {
 
 constexpr int kWarps = 4;
+constexpr int kMaxWords = 64;  // words per bit plane: 59 for the planar d = 31 code
 
 struct SampleArgs {
   DevCode code;
@@ -24,7 +25,7 @@ struct SampleArgs {
 };
 
 __global__ void __launch_bounds__(kWarps * 32) sample_kernel(const __grid_constant__ SampleArgs A) {
-  __shared__ uint32_t planes[kWarps][2 * 32];
+  __shared__ uint32_t planes[kWarps][2 * kMaxWords];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t k = (int64_t)blockIdx.x * kWarps + warp;
   if (k >= A.n_shots) return;
@@ -52,17 +53,31 @@ __global__ void __launch_bounds__(kWarps * 32) sample_kernel(const __grid_consta
     uint32_t* out = A.errors + (size_t)k * 2 * w;
     for (int i = lane; i < 2 * w; i += 32) out[i] = P[i];
   }
-  // s_f: X corners (TL, BR) see the Z bit, Z corners (TR, BL) see the X bit.
+  // s_f: X corners (rotated TL, BR; planar left, right) see the Z bit, Z
+  // corners (rotated TR, BL; planar up, down) see the X bit.
+  const bool planar = C.layout == kLayoutPlanar;
+  const int g = planar ? 2 * d - 1 : d;
   for (int base = 0; base < C.ns; base += 32) {
     const int f = base + lane;
     int bit = 0;
     if (f < C.ns) {
       const int a = C.face_a[f], b = C.face_b[f];
-      const int rr[4] = {a, a, a + 1, a + 1}, cc[4] = {b, b + 1, b, b + 1};
+      int rr[4], cc[4];
+      if (planar) {  // left, up, down, right
+        rr[0] = a; cc[0] = b - 1;
+        rr[1] = a - 1; cc[1] = b;
+        rr[2] = a + 1; cc[2] = b;
+        rr[3] = a; cc[3] = b + 1;
+      } else {  // TL, TR, BL, BR
+        rr[0] = a; cc[0] = b;
+        rr[1] = a; cc[1] = b + 1;
+        rr[2] = a + 1; cc[2] = b;
+        rr[3] = a + 1; cc[3] = b + 1;
+      }
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
-        if (rr[c] < 0 || rr[c] >= d || cc[c] < 0 || cc[c] >= d) continue;
-        const int q = rr[c] * d + cc[c];
+        if (rr[c] < 0 || rr[c] >= g || cc[c] < 0 || cc[c] >= g) continue;
+        const int q = planar ? planar_qubit(d, rr[c], cc[c]) : rr[c] * d + cc[c];
         const int plane = (c == 0 || c == 3) ? w : 0;
         bit ^= (P[plane + (q >> 5)] >> (q & 31)) & 1;
       }

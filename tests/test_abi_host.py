@@ -44,7 +44,7 @@ def test_argument_validation(X):
             X.Code(d)
         assert e.value.status == XZZX_EINVAL
     with pytest.raises(XzzxError) as e:
-        X.Code(5, layout=1)
+        X.Code(5, layout=2)
     assert e.value.status == XZZX_EUNSUPPORTED
     for bad in ((0.0, 0.1, 0.1), (0.3, 0.2, 0.1), (-0.1, 0.1, 0.1)):
         with pytest.raises(XzzxError):
@@ -70,6 +70,22 @@ def test_faces_match_oracle(X, d):
     assert c.words == (d * d + 31) // 32 and c.syn_words == (d * d - 1 + 31) // 32
 
 
+@pytest.mark.parametrize("d", [3, 5, 11, 21, 31])
+def test_planar_faces_match_oracle(X, d):
+    """The library's planar tables (face sites, corner qubits, colour classes,
+    index order) equal the oracle's pinned ones."""
+    c = X.Code(d, layout=X.LAYOUT_PLANAR)
+    a, b, corners = c.faces()
+    cid = O.planar(d)
+    of = O.code_faces(cid)
+    assert np.array_equal(a, of["a"]) and np.array_equal(b, of["b"])
+    assert np.array_equal(corners, of["corners"])
+    nq, ns, cs = O.code_sizes(cid)
+    assert c.colour_start == list(cs)
+    assert c.n_qubits == nq and c.n_stab == ns
+    assert c.words == (nq + 31) // 32 and c.syn_words == (ns + 31) // 32
+
+
 @pytest.mark.parametrize("p,eta,conv,scale", [(0.10, 10, 0, 1024), (0.10, 100, 0, 1024), (0.22, 100, 0, 1024),
                                               (0.15, 1000, 0, 4096), (0.30, 1000, 0, 4096), (0.2, 1.0, 1, 1024),
                                               (0.12, 5, 1, 2048)])
@@ -82,10 +98,12 @@ def test_weights_match_oracle(X, p, eta, conv, scale):
 
 
 def reachable_positive_dE(W4):
-    """Every energy change a bulk or boundary generator can make (brute force)."""
+    """Every energy change a generator can make (brute force): the bulk X Z Z X
+    face, the rotated weight-2 faces and the planar three-body faces (X X Z
+    and X Z Z)."""
     flip = [2, 1, 1, 2]
     out = set()
-    for mask in (0xF, 0xC, 0x3, 0xA, 0x5):
+    for mask in (0xF, 0xC, 0x3, 0xA, 0x5, 0xB, 0x7):
         corners = [k for k in range(4) if (mask >> k) & 1]
         for labs in np.ndindex(*([4] * len(corners))):
             dE = sum(int(W4[l ^ flip[k]]) - int(W4[l]) for k, l in zip(corners, labs))
