@@ -454,12 +454,13 @@ def run_ler(args):
     import paper_2509_17837_gb300 as X
     from paper_2509_17837_gb300 import stats
     NSA, NB, shots, chunk = 100, 100, args.ler_shots, 25000
+    layout = X.LAYOUT_PLANAR if args.layout == "planar" else X.LAYOUT_ROTATED
     forms = {"colour": (X.ORDER_COLOUR, X.EMIN_PER_PHASE), "literal": (X.ORDER_RANDOM_SITE, X.EMIN_PER_ATTEMPT)}
     curves, anneal_ms, attempts, total_shots = {}, {k: 0.0 for k in forms}, {k: 0 for k in forms}, 0
     t_wall = time.perf_counter()
     for eta, ps in LER_GRID.items():
         for d in LER_D:
-            code = X.Code(d)
+            code = X.Code(d, layout)
             for pi, p in enumerate(ps):
                 noise = X.noise_from_eta(p, eta, X.CONVENTION_PAPER, 1024)
                 sched = X.Schedule(noise, NB, 0.9, 1.0, X.PAPER_LOG)
@@ -477,7 +478,7 @@ def run_ler(args):
                         r = X.decode_reduce(code, init, cb, a["best_E"], true_errors=err)
                         fails += int(r["fail"].sum())
                         anneal_ms[form] += e0.elapsed_time(e1)
-                    attempts[form] += shots * NSA * 4 * NB * (d * d - 1)
+                    attempts[form] += shots * NSA * 4 * NB * code.n_stab
                     total_shots += shots
                     curves.setdefault(form, {}).setdefault("%g" % eta, {}).setdefault(str(d), []).append(
                         stats.ler_record(p, fails, shots))
@@ -490,8 +491,9 @@ def run_ler(args):
         "value": total_shots / wall, "unit": "decoded shots/s (whole sweep, wall clock)", "n_gpus": 1,
         "steps": 1, "warmup": 0, "ms_per_step": wall * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (library sampler, seeded)",
-        "config": {"workload": "d in {5,7,9}, eta in {1,5,10} (px:py:pz = 1:eta:1), 7 values of p each, %d shots "
-                               "per point, N_SA=100, N_beta=100, log schedule 0.9->1.0 beta_N" % shots,
+        "config": {"workload": "%s lattice, d in {5,7,9}, eta in {1,5,10} (px:py:pz = 1:eta:1), 7 values of p each, "
+                               "%d shots per point, N_SA=100, N_beta=100, log schedule 0.9->1.0 beta_N"
+                               % (args.layout, shots),
                    "forms": {"colour": "colour sweep, minimum per colour phase",
                              "literal": "random generator per attempt, minimum per attempt (Alg. 2 / Alg. 3)"}},
         "anneal_attempts_per_s": {k: attempts[k] / (anneal_ms[k] / 1e3) for k in forms},
@@ -513,6 +515,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", default="d11", choices=["d11", "uneven", "serve", "large", "ler"])
     ap.add_argument("--ler-shots", type=int, default=100000)
+    ap.add_argument("--layout", default="rotated", choices=["rotated", "planar"])
     ap.add_argument("--large-shots-per-p", type=int, default=57)
     ap.add_argument("--uneven-shots", type=int, default=60000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
