@@ -281,10 +281,19 @@ __global__ void __launch_bounds__(kPThreads) anneal_planar_kernel(const __grid_c
 
 }  // namespace
 
-// Launch for a planar code (arguments checked by the caller).
+xzzx_status launch_anneal_planar_reg(const xzzx_code* code, const xzzx_schedule* sched, uint64_t seed, uint64_t shot0,
+                                     int n_shots, int restarts, const uint32_t* init, int32_t* best_E,
+                                     uint32_t* best_cfg, int32_t* final_E, uint32_t* final_cfg, cudaStream_t stream);
+
+// Launch for a planar code (arguments checked by the caller): the colour sweep
+// with per-phase minima runs register-resident up to d = 15, everything else
+// in the table-driven kernel below.
 xzzx_status launch_anneal_planar(const xzzx_code* code, const xzzx_schedule* sched, uint64_t seed, uint64_t shot0,
                                  int n_shots, int restarts, int order, int emin, const uint32_t* init, int32_t* best_E,
                                  uint32_t* best_cfg, int32_t* final_E, uint32_t* final_cfg, cudaStream_t stream) {
+  if (order == 0 && emin == 0 && code->d <= 15)
+    return launch_anneal_planar_reg(code, sched, seed, shot0, n_shots, restarts, init, best_E, best_cfg, final_E,
+                                    final_cfg, stream);
   PlanarArgs A;
   A.keys = philox_keys(seed);
   A.chain0 = shot0 * (uint64_t)restarts * 4u;
