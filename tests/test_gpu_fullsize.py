@@ -1,0 +1,98 @@
+"""Parity at full size, in the launch configuration the benchmark times.
+
+The d = 11 workload runs one launch of 20,000 shots x 64 restarts (256 chains
+per shot, 1000 sweeps) exactly as a benchmark step does, and a sample of its
+shots is decoded by the oracle one by one: classes, coset energies, every
+chain's minimum energy, recoveries and failure flags must agree bit for bit.
+The d = 31 workload (256 restarts, 1e4 sweeps, one launch of 57 shots) is too
+large for the oracle to decode a whole shot, so sampled references and chains
+are checked one by one and the decision is checked against the GPU's own chain
+energies (the coset minima follow from them by Eq. coset_correspondence).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from layout import words_to_labels
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def X():
+    from paper_2509_17837_gb300 import build
+    build.build()
+    import paper_2509_17837_gb300 as X
+    return X
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+    return torch
+
+
+def test_d11_bench_launch_sampled_shots(X, torch):
+    import bench
+    d, R, S = bench.D, bench.RESTARTS, 20000
+    pi, p = 2, bench.PS[2]
+    seed = bench.SEED + pi
+    code = X.Code(d)
+    noise = X.noise_from_eta(p, bench.ETA, 0, bench.SCALE)
+    sched = X.Schedule(noise, bench.SWEEPS, bench.BETA0, bench.BETA1)
+    shot0 = bench.rank_shot_base(0, 8, S) + 3 * S          # step 3 of rank 0
+    err, syn = X.sample_errors(code, noise, seed, shot0, S)
+    init, cbits = X.greedy_init(code, noise, seed, shot0, syn, R)
+    a = X.anneal(code, sched, seed, shot0, init, want_cfg=False)
+    out = X.decode_reduce(code, init, cbits, a["best_E"], true_errors=err)
+    torch.cuda.synchronize()
+    pxyz = (noise.px, noise.py, noise.pz)
+    rng = np.random.default_rng(11)
+    picks = sorted({0, 1, S // 2, S - 1, *rng.integers(0, S, 2).tolist()})
+    oerr, osyn = O.sample(d, pxyz, seed, shot0, 1)  # the sampler is checked elsewhere; spot-check one row
+    assert np.array_equal(words_to_labels(err[0].cpu().numpy(), d * d), oerr[0])
+    best_E = a["best_E"].cpu().numpy()
+    for s in picks:
+        oe, os_ = O.sample(d, pxyz, seed, shot0 + s, 1)
+        ref = O.decode(d, pxyz, bench.SCALE, O.LINEAR, bench.SWEEPS, bench.BETA0, bench.BETA1, seed, shot0 + s, R,
+                       os_, oe, want_chains=True)
+        assert int(out["cls"][s]) == int(ref["cls"][0]), s
+        assert np.array_equal(out["E4"][s].cpu().numpy(), ref["E4"][0]), s
+        assert np.array_equal(best_E[s].reshape(-1), ref["chain_E"][0]), s
+        assert np.array_equal(words_to_labels(out["recovery"][s].cpu().numpy(), d * d), ref["recovery"][0]), s
+        assert int(out["fail"][s]) == int(ref["fail"][0]), s
+
+
+def test_d31_bench_launch_sampled_chains(X, torch):
+    import bench
+    d, R, N, b0, b1, scale, eta, seed = 31, 256, 10000, 0.02, 30.0, 4096, 1000.0, 0xD31
+    S, p = 57, bench.LARGE_PS[0]
+    code = X.Code(d)
+    noise = X.noise_from_eta(p, eta, 0, scale)
+    sched = X.Schedule(noise, N, b0, b1)
+    err, syn = X.sample_errors(code, noise, seed, 0, S)
+    init, cbits = X.greedy_init(code, noise, seed, 0, syn, R)
+    a = X.anneal(code, sched, seed, 0, init, want_cfg=False)
+    out = X.decode_reduce(code, init, cbits, a["best_E"], true_errors=err)
+    torch.cuda.synchronize()
+    pxyz = (noise.px, noise.py, noise.pz)
+    init_h, cb_h = init.cpu().numpy(), cbits.cpu().numpy()
+    best_E = a["best_E"].cpu().numpy()
+    LX, LZ = O.logicals(d)
+    Ls = [0 * LX, LX, LX ^ LZ, LZ]
+    for s, i, P in [(0, 0, 0), (0, 255, 2), (28, 17, 1), (56, 128, 3)]:
+        _, os_ = O.sample(d, pxyz, seed, s, 1)
+        Ri, _ = O.greedy(d, pxyz, scale, seed, s, i, 1, os_[0])
+        assert np.array_equal(words_to_labels(init_h[s, i], d * d), Ri), (s, i)
+        assert cb_h[s, i] & 3 == O.class_bits(d, Ri)
+        chain = (s * R + i) * 4 + P
+        ref = O.anneal_chain(d, pxyz, scale, O.LINEAR, N, b0, b1, seed, chain, Ri ^ Ls[P])
+        assert best_E[s, i, P] == ref["best_E"], (s, i, P)
+    # the decision from the GPU's own chain energies (Eqs. coset_correspondence, determine_P_from_E)
+    to_bits = [0, 1, 3, 2]
+    for s in range(S):
+        q = (cb_h[s] & 3) ^ (cb_h[s, 0] & 3)
+        E4 = [min(int(best_E[s, i, Pc]) for i in range(R) for Pc in range(4)
+                  if to_bits.index(q[i] ^ to_bits[Pc]) == P) for P in range(4)]
+        assert list(out["E4"][s].cpu().numpy()) == E4
+        assert int(out["cls"][s]) == int(np.argmin(E4))
