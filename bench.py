@@ -314,7 +314,7 @@ def run_serve(args):
     import paper_2509_17837_gb300 as X
     seed, R, N = 0x5E5E, 32, 1000
     sv = X.Server(seed, R, N, BETA0, BETA1, max_batch=args.serve_max_batch, n_slots=args.serve_slots,
-                  queue_capacity=1 << 22, hbm_budget_bytes=1 << 30)
+                  queue_capacity=1 << 22, hbm_budget_bytes=1 << 30, resident_waves=args.serve_waves)
     noise = X.noise_from_eta(0.15, ETA)
     cids = [sv.add_class(d, noise) for d in SERVE_DS]
     sv.start()
@@ -363,7 +363,8 @@ def run_serve(args):
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (library sampler, seeded; Poisson arrivals)",
         "config": {"workload": "serving: Poisson single-shot requests, d uniform over {5,9,13,17,21,25}, eta=100, "
                                "p=0.15, 32 restarts, 1000 sweeps, linear beta 0.05->20",
-                   "max_batch": args.serve_max_batch, "slots": args.serve_slots, "hbm_budget_bytes": 1 << 30},
+                   "max_batch": args.serve_max_batch, "slots": args.serve_slots, "hbm_budget_bytes": 1 << 30,
+                   "resident_waves": args.serve_waves or 2},
         "points": points, "saturation_move_attempts_per_s": sat["throughput_req_per_s"] * mean_att}))
 
 
@@ -519,9 +520,10 @@ def main():
     ap.add_argument("--large-shots-per-p", type=int, default=57)
     ap.add_argument("--uneven-shots", type=int, default=60000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
-    ap.add_argument("--serve-max-requests", type=int, default=6000)
+    ap.add_argument("--serve-max-requests", type=int, default=30000)
     ap.add_argument("--serve-max-batch", type=int, default=1024)
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-waves", type=int, default=0)
     args = ap.parse_args()
     if args.workload == "uneven" and args.impl == "ours":
         return run_uneven(args)

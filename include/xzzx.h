@@ -321,6 +321,11 @@ typedef struct {
                                chain (lower latency) while the warps of all batches doing so
                                stay within 16 per SM; otherwise one thread per chain, which
                                has the higher throughput (0 = 16, -1 = never) */
+  int32_t resident_waves;   /* register budget of all batches in flight, in GPU-fulls of the
+                               annealing kernels' resident CTAs (0 = 2).  1: every admitted
+                               request is resident at once; 2 or more lets CTAs queue in hardware
+                               behind running ones, which keeps the GPU busy between batches
+                               under heavy load (light loads form small batches either way) */
 } xzzx_serve_cfg;
 
 typedef struct {
@@ -342,8 +347,9 @@ typedef struct xzzx_server xzzx_server;
  * Code tables, schedules and a pool of in-flight slots stay on the current
  * device.  A dispatcher thread forms a batch whenever a slot is free, taking
  * pending requests in arrival order (one distance per batch) while they
- * fit the slot's memory and the GPU's register budget, decodes it with the
- * batched launches, and overlaps batches of different slots on the GPU.
+ * fit the slot's memory and the register budget (resident_waves), decodes it
+ * with the batched launches (the batch distance's own annealing kernel), and
+ * overlaps batches of different slots on the GPU.
  * Requests that arrive while others run are admitted as slots and budget free
  * up.  A request's result depends only on (seed, request id, class,
  * syndrome), never on the batch it shared.  All host waits are bounded. */

@@ -52,7 +52,8 @@ class ServeCfg(C.Structure):
     _fields_ = [("seed", C.c_uint64), ("restarts", C.c_int32), ("n_sweeps", C.c_int32),
                 ("sched_kind", C.c_int32), ("beta0", C.c_double), ("beta1", C.c_double),
                 ("max_batch", C.c_int32), ("n_slots", C.c_int32), ("queue_capacity", C.c_int32),
-                ("hbm_budget_bytes", C.c_size_t), ("warp_max_requests", C.c_int32)]
+                ("hbm_budget_bytes", C.c_size_t), ("warp_max_requests", C.c_int32),
+                ("resident_waves", C.c_int32)]
 
 
 class Result(C.Structure):

@@ -290,9 +290,9 @@ class Server:
     """
 
     def __init__(self, seed, restarts, n_sweeps, beta0, beta1, kind=LINEAR, max_batch=256, n_slots=4,
-                 queue_capacity=1 << 20, hbm_budget_bytes=0, warp_max_requests=0):
+                 queue_capacity=1 << 20, hbm_budget_bytes=0, warp_max_requests=0, resident_waves=0):
         cfg = ServeCfg(seed, restarts, n_sweeps, kind, beta0, beta1, max_batch, n_slots, queue_capacity,
-                       hbm_budget_bytes, warp_max_requests)
+                       hbm_budget_bytes, warp_max_requests, resident_waves)
         h = C.c_void_p()
         call("xzzx_serve_create", C.byref(cfg), C.byref(h))
         self._h = h

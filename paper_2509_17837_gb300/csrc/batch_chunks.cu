@@ -20,6 +20,27 @@ static xzzx_status configure_chunks_d() {
   return XZZX_OK;
 }
 
+template <int D>
+static xzzx_status occupancy_chunks_d(int* ctas_per_sm) {
+  constexpr size_t smem = core::smem_bytes<D, kNT>();
+  XZZX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, anneal_chunks_kernel<D>, kNT, smem));
+  return XZZX_OK;
+}
+
+xzzx_status occupancy_chunks(int d, int* ctas_per_sm) {
+  switch (d) {
+#define XZZX_CASE(DD) \
+  case DD:            \
+    return occupancy_chunks_d<DD>(ctas_per_sm);
+    XZZX_CASE(3) XZZX_CASE(5) XZZX_CASE(7) XZZX_CASE(9) XZZX_CASE(11) XZZX_CASE(13) XZZX_CASE(15)
+    XZZX_CASE(17) XZZX_CASE(19) XZZX_CASE(21) XZZX_CASE(23) XZZX_CASE(25) XZZX_CASE(27) XZZX_CASE(29)
+    XZZX_CASE(31)
+#undef XZZX_CASE
+    default:
+      return fail(XZZX_EUNSUPPORTED, "no annealing kernel for this distance");
+  }
+}
+
 xzzx_status launch_chunks(int d, const AnnealLaunch& L, cudaStream_t stream) {
   switch (d) {
 #define XZZX_CASE(DD) \

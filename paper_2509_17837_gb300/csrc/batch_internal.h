@@ -95,6 +95,8 @@ xzzx_status configure_plan_kernels(int dmax, int* ctas_per_sm);
 
 // Per-distance chunk kernel (one CTA per chunk).
 xzzx_status launch_chunks(int d, const AnnealLaunch& L, cudaStream_t stream);
+// Resident CTAs per SM of the distance-d chunk kernel (configured first).
+xzzx_status occupancy_chunks(int d, int* ctas_per_sm);
 
 // Per-distance warp-per-chain kernel over the chains [chain0, chain0 + n).
 struct WarpLaunch {

@@ -7,11 +7,13 @@
 //
 // A dispatcher thread forms a batch whenever a slot is free: it takes pending
 // requests in arrival order (of one distance, so the batch's work finishes
-// together) while they fit the slot's memory and the
-// GPU's register budget, so that every admitted request's CTAs can be resident
-// at once.  The batch is decoded by the batched plan (one greedy launch, one
-// persistent annealing launch, one decision launch; small batches on a lightly
-// loaded GPU anneal with one warp per chain instead, for latency) between a
+// together) while they fit the slot's memory and the register budget: a
+// number of GPU-fulls of the kernels' resident CTAs (two by default, so that
+// under load the next batch's CTAs already wait in hardware when a batch
+// ends).  The batch is decoded by the batched plan (one greedy launch, one
+// annealing launch of the batch distance's own kernel, one decision launch;
+// small batches on a lightly loaded GPU anneal with one warp per chain
+// instead, for latency) between a
 // host-to-device
 // copy of the syndromes and a device-to-host copy of the results; batches in
 // different slots overlap on the GPU.  A host callback on the slot's stream
@@ -176,7 +178,10 @@ xzzx_status issue(xzzx_server* sv, Slot& slot) {
   XZZX_CUDA_TRY(cudaMemcpyAsync(slot.dev, slot.host_in, desc, cudaMemcpyHostToDevice, slot.stream));
   XZZX_CUDA_TRY(cudaMemcpyAsync(slot.dev + o_syn, slot.host_in + o_syn, syn_bytes, cudaMemcpyHostToDevice,
                                 slot.stream));
-  if ((st = launch_plan(plan, pd, sv->keys, (int)plan.lpt.size(), slot.warp_mode ? 2 : 0, slot.stream))) return st;
+  // One distance per batch: its own chunk kernel (mode 1) runs with that
+  // distance's register allocation; the persistent form's queue over distances
+  // has nothing to balance here.
+  if ((st = launch_plan(plan, pd, sv->keys, (int)plan.lpt.size(), slot.warp_mode ? 2 : 1, slot.stream))) return st;
   XZZX_CUDA_TRY(cudaMemcpyAsync(slot.host_out, slot.dev + o_out, out_bytes, cudaMemcpyDeviceToHost, slot.stream));
   XZZX_CUDA_TRY(cudaLaunchHostFunc(slot.stream, on_complete, &slot));
   return XZZX_OK;
@@ -328,6 +333,7 @@ xzzx_status xzzx_serve_create(const xzzx_serve_cfg* cfg, xzzx_server** out) {
   if (cfg->max_batch < 1 || cfg->max_batch > 4096 || cfg->n_slots < 1 || cfg->n_slots > 64)
     return fail(XZZX_EINVAL, "max_batch must be in [1, 4096] and n_slots in [1, 64]");
   if (cfg->queue_capacity < 1) return fail(XZZX_EINVAL, "queue_capacity must be positive");
+  if (cfg->resident_waves < 0 || cfg->resident_waves > 64) return fail(XZZX_EINVAL, "resident_waves must be in [0, 64]");
   xzzx_server* sv = new (std::nothrow) xzzx_server();
   if (!sv) return fail(XZZX_ENOMEM, "host allocation");
   sv->cfg = *cfg;
@@ -374,14 +380,15 @@ xzzx_status xzzx_serve_start(xzzx_server* sv) {
   if (sv->classes.empty()) return fail(XZZX_EINVAL, "no classes registered");
   xzzx_status st = check_device(sv->device);
   if (st) return st;
-  // On-chip budget: a request's CTAs take the share of an SM that the
-  // annealing kernel its distance runs (d <= 15, <= 21, <= 31) occupies.
+  // On-chip budget: a request's CTAs take the share of an SM that its
+  // distance's chunk kernel occupies.
   int regs_per_sm = 0;
   XZZX_CUDA_TRY(cudaDeviceGetAttribute(&regs_per_sm, cudaDevAttrMaxRegistersPerMultiprocessor, sv->device));
-  sv->regs_total = (int64_t)regs_per_sm * sv->n_sm;
+  sv->regs_total = (int64_t)regs_per_sm * sv->n_sm * (sv->cfg.resident_waves > 0 ? sv->cfg.resident_waves : 2);
   for (Class& c : sv->classes) {
     int per_sm = 0;
     if ((st = batch::configure_plan_kernels(c.d, &per_sm))) return st;
+    if ((st = batch::occupancy_chunks(c.d, &per_sm))) return st;
     if (per_sm < 1) per_sm = 1;
     const int64_t ctas = (4 * (int64_t)sv->cfg.restarts + batch::kNT - 1) / batch::kNT;
     c.regs = ctas * (regs_per_sm / per_sm);
