@@ -152,7 +152,9 @@ def run_reference(args):
         "value": att, "unit": "move-attempts/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic (library sampler, seeded)",
-        "config": workload_config(shots, 1), "shots_per_s": shots * args.steps / dt,
+        "config": dict(workload_config(shots, 1), global_batch=shots, parallelism="one host core (the oracle)",
+                       shots_per_p_per_step=None, sample=sample, l2="n/a (host)"),
+        "shots_per_s": shots * args.steps / dt,
         "cpu_baseline": {"value": att, "unit": "move-attempts/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": att, "unit": "move-attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 

@@ -51,11 +51,12 @@ template <int D>
 xzzx_status launch_d(const AnnealArgs& A, cudaStream_t stream) {
   constexpr int NT = Shape<D>::kThreads;
   const size_t smem = smem_bytes<D, NT>();
-  static bool configured = false;  // attribute is per function and device-independent
-  if (!configured) {
+  static DeviceOnce once;
+  xzzx_status st = once.run([&]() -> xzzx_status {
     XZZX_CUDA_TRY(cudaFuncSetAttribute(anneal_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = true;
-  }
+    return XZZX_OK;
+  });
+  if (st) return st;
   const int64_t grid = (A.n_chains + NT - 1) / NT;
   if (grid > 0x7FFFFFFF) return fail(XZZX_EINVAL, "too many chains for one launch");
   anneal_kernel<D><<<(unsigned)grid, NT, smem, stream>>>(A);

@@ -318,12 +318,13 @@ xzzx_status launch_anneal_planar(const xzzx_code* code, const xzzx_schedule* sch
   A.final_E = final_E;
   A.final_cfg = final_cfg;
   const size_t smem = planar_smem_bytes(A.d, A.m);
-  static bool configured = false;  // the attribute is per function, not per device
-  if (!configured) {
+  static DeviceOnce once;
+  xzzx_status st = once.run([&]() -> xzzx_status {
     const int most = (int)planar_smem_bytes(kMaxD, 2 * kMaxD * (kMaxD - 1));
     XZZX_CUDA_TRY(cudaFuncSetAttribute(anneal_planar_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, most));
-    configured = true;
-  }
+    return XZZX_OK;
+  });
+  if (st) return st;
   const int64_t grid = (A.n_chains + kPThreads - 1) / kPThreads;
   if (grid > 0x7FFFFFFF) return fail(XZZX_EINVAL, "too many chains for one launch");
   anneal_planar_kernel<<<(unsigned)grid, kPThreads, smem, stream>>>(A);

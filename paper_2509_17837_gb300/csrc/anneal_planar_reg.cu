@@ -280,12 +280,13 @@ __global__ void __launch_bounds__(kRThreads) anneal_planar_reg_kernel(const __gr
 template <int D>
 xzzx_status launch_d(const RegArgs& A, cudaStream_t stream) {
   const size_t smem = reg_smem_bytes<D>();
-  static bool configured = false;
-  if (!configured) {
+  static DeviceOnce once;
+  xzzx_status st = once.run([&]() -> xzzx_status {
     XZZX_CUDA_TRY(cudaFuncSetAttribute(anneal_planar_reg_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem));
-    configured = true;
-  }
+    return XZZX_OK;
+  });
+  if (st) return st;
   const int64_t grid = (A.n_chains + kRThreads - 1) / kRThreads;
   if (grid > 0x7FFFFFFF) return fail(XZZX_EINVAL, "too many chains for one launch");
   anneal_planar_reg_kernel<D><<<(unsigned)grid, kRThreads, smem, stream>>>(A);

@@ -307,12 +307,13 @@ extern "C" xzzx_status xzzx_anneal_variant(const xzzx_code* code, const xzzx_sch
   A.final_E = final_E;
   A.final_cfg = final_cfg;
   const size_t smem = variant_smem_bytes(A.d, A.m);
-  static int configured_bytes = 0;  // the attribute is per function, not per device
-  if ((int)smem > configured_bytes) {
-    XZZX_CUDA_TRY(cudaFuncSetAttribute(anneal_variant_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)variant_smem_bytes(kMaxD, kMaxD * kMaxD - 1)));
-    configured_bytes = (int)variant_smem_bytes(kMaxD, kMaxD * kMaxD - 1);
-  }
+  static DeviceOnce once;
+  if ((st = once.run([&]() -> xzzx_status {
+         XZZX_CUDA_TRY(cudaFuncSetAttribute(anneal_variant_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)variant_smem_bytes(kMaxD, kMaxD * kMaxD - 1)));
+         return XZZX_OK;
+       })))
+    return st;
   const int64_t grid = (A.n_chains + kVarThreads - 1) / kVarThreads;
   if (grid > 0x7FFFFFFF) return fail(XZZX_EINVAL, "too many chains for one launch");
   anneal_variant_kernel<<<(unsigned)grid, kVarThreads, smem, (cudaStream_t)stream>>>(A);

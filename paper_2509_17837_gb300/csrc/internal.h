@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -17,6 +18,28 @@ namespace xzzx {
 xzzx_status fail(xzzx_status st, const std::string& msg);
 xzzx_status ok();
 xzzx_status cuda_fail(cudaError_t e, const char* what);
+
+// One-time setup per device (a kernel's dynamic shared memory limit belongs to
+// the device context it is set on).  Two threads may both run the setup; it
+// is idempotent.
+class DeviceOnce {
+ public:
+  // Runs fn() unless it already ran for the current device.
+  template <typename F>
+  xzzx_status run(F fn) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    const uint64_t bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done_.load(std::memory_order_acquire) & bit)) return XZZX_OK;
+    xzzx_status st = fn();
+    if (st == XZZX_OK && bit) done_.fetch_or(bit, std::memory_order_acq_rel);
+    return st;
+  }
+
+ private:
+  std::atomic<uint64_t> done_{0};
+};
 
 #define XZZX_CUDA_TRY(expr)                                    \
   do {                                                         \
