@@ -247,8 +247,12 @@ def run_uneven(args):
     segs = uneven_segments(X, args.uneven_shots, seed)
     tune_segs = uneven_segments(X, args.uneven_shots, seed, scale_shots=0.125)
     cfg, timings = autotune.tune(lambda c, o: X.Batch(tune_segs, seed, ctas_per_sm=c, order=o), tune_segs,
-                                 candidates=[(0, 0), (0, 1), (1, 0), (2, 0), (3, 0)], use_cache=False)
-    batch = X.Batch(segs, seed, ctas_per_sm=cfg[0], order=cfg[1])
+                                 candidates=[(0, 0, 0), (0, 0, 1), (0, 1, 0), (0, 2, 0), (0, 3, 0), (1, 0, 0),
+                                             (2, 0, 0)], use_cache=False)
+    # the persistent launch (the form this workload measures) with the tuned grid and order
+    best_persistent = min((k for k in timings if k.startswith("0,")), key=timings.get)
+    _, cps, order = (int(x) for x in best_persistent.split(","))
+    batch = X.Batch(segs, seed, ctas_per_sm=cps, order=order)
     info = batch.info()
     stream = torch.cuda.Stream()
     dev = torch.cuda.current_device()
@@ -290,8 +294,11 @@ def run_uneven(args):
                                "p in [0.08,0.20] (0.005 grid), restarts {16,16,32,32,64,64}, sweeps "
                                "{500,500,1000,1000,2000,2000}, linear beta 0.05->20" % shots,
                    "segments": info["n_segments"], "chunks": info["n_chunks"],
-                   "persistent_grid": info["persistent_grid"], "autotuned_cfg": {"ctas_per_sm": cfg[0],
-                                                                                   "order": cfg[1]},
+                   "persistent_grid": info["persistent_grid"],
+                   "autotuned_cfg": {"mode": cfg[0], "ctas_per_sm": cfg[1], "order": cfg[2],
+                                     "modes": "0 persistent thread/chain, 1 per-distance thread/chain, "
+                                              "2 per-distance warp/chain"},
+                   "persistent_cfg": {"ctas_per_sm": cps, "order": order},
                    "autotune_s": timings, "l2": "flushed between steps"},
         "move_attempts_per_s": att, "plain_ms_per_step": ms_plain, "plain_shots_per_s": shots / (ms_plain / 1e3),
         "speedup_vs_plain": ms_plain / ms_batched, "identical_outputs": bool(same),

@@ -1,66 +1,93 @@
-"""Autotuner for batched decoding: picks the persistent grid (CTAs per SM) and
-the chunk-queue order for a batch shape by timing short runs, and caches the
-choice in a JSON file keyed by GPU name and batch shape.
+"""Autotuner for batched decoding.
 
-The knobs only change scheduling: every choice decodes bit-identically.
+It picks, for a batch shape, by timing short runs:
+
+* the chain-to-hardware mapping, as the launch mode of ``Batch.run``:
+  0 = one persistent launch, one chain per thread, CTAs pulling chunks of
+  chains from a queue; 1 = one launch per distance, one chain per thread;
+  2 = one launch per distance, one chain per warp;
+* for mode 0, the persistent grid in CTAs per SM (how many chains are in
+  flight per SM; 0 = the occupancy limit) and the order of the chunk queue
+  (0 = longest chunks first, 1 = segment order).
+
+The choice is cached in a JSON file keyed by GPU name and batch shape.  The
+knobs only change scheduling: every choice decodes bit-identically.  (The
+chains per CTA of each kernel and the unroll of its sweep loop are fixed at
+compile time at the values measured fastest.)
 """
 import json
 import os
 import time
 
-import torch
-
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
+KEY_VERSION = "v2"
+
+# (mode, ctas_per_sm, order)
+DEFAULT_CANDIDATES = [(0, c, o) for c in (0, 1, 2, 3, 4) for o in (0, 1)] + [(1, 0, 0), (2, 0, 0)]
 
 
-def _load():
+def _load(path):
     try:
-        with open(CACHE) as f:
+        with open(path) as f:
             return json.load(f)
     except (OSError, ValueError):
         return {}
 
 
-def _save(cache):
-    tmp = CACHE + ".tmp.%d" % os.getpid()
+def _save(path, cache):
+    tmp = path + ".tmp.%d" % os.getpid()
     with open(tmp, "w") as f:
         json.dump(cache, f, indent=1, sort_keys=True)
-    os.replace(tmp, CACHE)
+    os.replace(tmp, path)
 
 
-def shape_key(segments):
+def shape_key(segments, device_name):
     """Batch shape: distances, restarts, sweeps and shot counts (not the data)."""
     parts = sorted((sg["code"].d, sg["restarts"], sg["sched"].n_sweeps) for sg in segments)
     shots = sum(int(sg["syndromes"].shape[0]) for sg in segments)
     dist = {}
     for d, r, n in parts:
         dist[(d, r, n)] = dist.get((d, r, n), 0) + 1
-    return "%s|%s|shots=%d" % (torch.cuda.get_device_name(), sorted(dist.items()), shots)
+    return "%s|%s|%s|shots=%d" % (KEY_VERSION, device_name, sorted(dist.items()), shots)
 
 
-def tune(make_batch, segments, candidates=None, reps=1, use_cache=True):
-    """make_batch(ctas_per_sm, order) -> Batch.  Returns (best_cfg, timings)."""
-    key = shape_key(segments)
-    cache = _load() if use_cache else {}
+_CURRENT = object()
+
+
+def tune(make_batch, segments, candidates=None, reps=1, use_cache=True, cache_path=None, device_name=None,
+         stream=_CURRENT, sync=None):
+    """Time each candidate (mode, ctas_per_sm, order) and return (best, timings).
+
+    make_batch(ctas_per_sm, order) -> an object with run(mode, stream) and
+    close().  stream / sync default to the current CUDA stream and
+    torch.cuda.synchronize; device_name to the current GPU's name.
+    """
+    if device_name is None or stream is _CURRENT or sync is None:
+        import torch
+        device_name = device_name or torch.cuda.get_device_name()
+        stream = torch.cuda.current_stream() if stream is _CURRENT else stream
+        sync = sync or torch.cuda.synchronize
+    path = cache_path or CACHE
+    key = shape_key(segments, device_name)
+    cache = _load(path) if use_cache else {}
     if use_cache and key in cache:
         return tuple(cache[key]["cfg"]), cache[key].get("timings", {})
-    if candidates is None:
-        candidates = [(c, o) for c in (0, 1, 2, 3, 4) for o in (0, 1)]
     timings = {}
-    stream = torch.cuda.current_stream()
-    for cps, order in candidates:
+    for mode, cps, order in (candidates or DEFAULT_CANDIDATES):
         b = make_batch(cps, order)
-        b.run(0, stream)  # warm-up
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(reps):
-            b.run(0, stream)
-        torch.cuda.synchronize()
-        timings["%d,%d" % (cps, order)] = (time.perf_counter() - t0) / reps
-        b.close()
+        try:
+            b.run(mode, stream)  # warm-up
+            sync()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                b.run(mode, stream)
+            sync()
+            timings["%d,%d,%d" % (mode, cps, order)] = (time.perf_counter() - t0) / reps
+        finally:
+            b.close()
     best = min(timings, key=timings.get)
     cfg = tuple(int(x) for x in best.split(","))
     if use_cache:
         cache[key] = {"cfg": list(cfg), "timings": timings}
-        _save(cache)
+        _save(path, cache)
     return cfg, timings
