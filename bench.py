@@ -33,9 +33,10 @@ D, ETA, PS, RESTARTS, SWEEPS, BETA0, BETA1, SCALE = 11, 100.0, (0.10, 0.13, 0.16
 SEED = 0xD11
 I_ALG = 30  # integer instructions per move attempt in the algorithmic count
 # DRAM bytes (read + write) per chain of anneal_kernel<11>, from one ncu
-# capture of the current kernel (128,000 chains, 1.5373e6 B): each chain reads
-# its 32-byte reference (shared by its four cosets) and writes 4 bytes.
-ANNEAL_DRAM_BYTES_PER_CHAIN = 1.5373e6 / 128000
+# capture of the current kernel (128,000 chains, 1.4738e6 B): each chain reads
+# its 32-byte reference (shared by its four cosets) and writes 4 bytes, which
+# stay in L2.
+ANNEAL_DRAM_BYTES_PER_CHAIN = 1.4738e6 / 128000
 # ALU-pipe lane instructions per attempt of anneal_kernel<11> (ncu
 # sm__inst_executed_pipe_alu of the same capture x 32 / attempts); the ALU
 # pipe takes 16 lanes per clock per SM sub-partition.
