@@ -273,6 +273,7 @@ typedef struct {
 typedef struct {
   int32_t ctas_per_sm; /* persistent grid = SMs x this; 0 = the occupancy maximum */
   int32_t order;       /* chunk queue: 0 = longest chunks first, 1 = segment order */
+  int32_t graph_mode;  /* the mode xzzx_batch_run_graph captures: 0 or 3 */
 } xzzx_batch_cfg;
 
 typedef struct {
@@ -295,9 +296,13 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
  * persistent annealing launch whose CTAs pull chunks (longest first) from an
  * atomic counter, one decision launch.  mode 1: the three kernels once per
  * distance (the plain form).  mode 2: as mode 1 with one warp per chain
- * (xzzx_anneal_warp).  All modes give identical outputs. */
+ * (xzzx_anneal_warp).  mode 3: one greedy launch, then each distance's own
+ * annealing kernel on its own stream forked from this one (largest distance
+ * first, so the hardware fills one distance's tail with the next one's CTAs),
+ * joined back before one decision launch; the batch owns those streams.
+ * All modes give identical outputs. */
 xzzx_status xzzx_batch_run(xzzx_batch* b, int mode, void* stream);
-/* mode 0 captured into a CUDA graph on the first call (stream must not be the
+/* cfg->graph_mode (0 or 3) captured into a CUDA graph on the first call (stream must not be the
  * legacy default stream), replayed on every call. */
 xzzx_status xzzx_batch_run_graph(xzzx_batch* b, void* stream);
 xzzx_status xzzx_batch_get_info(const xzzx_batch* b, xzzx_batch_info* out);

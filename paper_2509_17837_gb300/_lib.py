@@ -39,7 +39,7 @@ class Segment(C.Structure):
 
 
 class BatchCfg(C.Structure):
-    _fields_ = [("ctas_per_sm", C.c_int32), ("order", C.c_int32)]
+    _fields_ = [("ctas_per_sm", C.c_int32), ("order", C.c_int32), ("graph_mode", C.c_int32)]
 
 
 class BatchInfo(C.Structure):

@@ -227,11 +227,13 @@ class Batch:
     segments: list of dicts with keys code, noise, sched, shot0, syndromes,
     restarts, and optionally randomised (default True) and true_errors.
     Output tensors (cls, E4, recovery, fail) are allocated per segment and
-    exposed as ``self.outputs``.  mode 0 = batched (persistent launch),
-    mode 1 = one launch per distance.
+    exposed as ``self.outputs``.  run(mode): 0 = one persistent launch,
+    1 = one launch per distance, 2 = as 1 with one warp per chain, 3 = the
+    distances' own launches concurrently on forked streams.  run_graph
+    replays graph_mode (0 or 3) as a captured CUDA graph.
     """
 
-    def __init__(self, segments, seed, ctas_per_sm=0, order=0):
+    def __init__(self, segments, seed, ctas_per_sm=0, order=0, graph_mode=0):
         self.segments = segments
         self.outputs = []
         arr = (Segment * len(segments))()
@@ -254,7 +256,7 @@ class Batch:
             a.E4 = out["E4"].data_ptr() if n else None
             a.recovery = out["recovery"].data_ptr() if n else None
             a.fail = out["fail"].data_ptr() if out["fail"] is not None and n else None
-        cfg = BatchCfg(ctas_per_sm, order)
+        cfg = BatchCfg(ctas_per_sm, order, graph_mode)
         h = C.c_void_p()
         call("xzzx_batch_create", arr, len(segments), seed, C.byref(cfg), C.byref(h))
         self._h = h

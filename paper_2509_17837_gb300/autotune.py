@@ -5,7 +5,8 @@ It picks, for a batch shape, by timing short runs:
 * the chain-to-hardware mapping, as the launch mode of ``Batch.run``:
   0 = one persistent launch, one chain per thread, CTAs pulling chunks of
   chains from a queue; 1 = one launch per distance, one chain per thread;
-  2 = one launch per distance, one chain per warp;
+  2 = one launch per distance, one chain per warp; 3 = each distance's own
+  launch, concurrently on forked streams;
 * for mode 0, the persistent grid in CTAs per SM (how many chains are in
   flight per SM; 0 = the occupancy limit) and the order of the chunk queue
   (0 = longest chunks first, 1 = segment order).
@@ -23,7 +24,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.jso
 KEY_VERSION = "v2"
 
 # (mode, ctas_per_sm, order)
-DEFAULT_CANDIDATES = [(0, c, o) for c in (0, 1, 2, 3, 4) for o in (0, 1)] + [(1, 0, 0), (2, 0, 0)]
+DEFAULT_CANDIDATES = [(0, c, o) for c in (0, 1, 2, 3, 4) for o in (0, 1)] + [(1, 0, 0), (2, 0, 0), (3, 0, 0)]
 
 
 def _load(path):

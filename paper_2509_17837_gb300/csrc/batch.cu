@@ -365,6 +365,12 @@ struct xzzx_batch {
   void* dev_block = nullptr;  // descriptors + workspace
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
+  int graph_mode = 0;
+  // mode 3: one side stream and one completion event per distance, and the
+  // fork event, created on first use
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -372,9 +378,48 @@ void free_batch(xzzx_batch* b) {
   if (!b) return;
   if (b->graph_exec) cudaGraphExecDestroy(b->graph_exec);
   if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->done) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
   if (b->dev_block) cudaFree(b->dev_block);
   delete b;
 }
+// Mode 3: greedy for all segments on `stream`, each distance's chunk kernel on
+// its own side stream (largest distance first), decisions after the join.
+xzzx_status launch_concurrent(xzzx_batch* b, cudaStream_t stream) {
+  using namespace xzzx::batch;
+  const Plan& p = b->plan;
+  const PlanDev& d = b->dev;
+  const size_t n = p.ranges.size();
+  while (b->side.size() < n) {
+    cudaStream_t s = nullptr;
+    XZZX_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    b->side.push_back(s);
+    cudaEvent_t e = nullptr;
+    XZZX_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    b->done.push_back(e);
+  }
+  if (!b->fork) XZZX_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+  xzzx_status st = run_greedy(p, d, b->keys, 0, p.total_ctas, stream);
+  if (st) return st;
+  XZZX_CUDA_TRY(cudaEventRecord(b->fork, stream));
+  for (size_t k = 0; k < n; ++k) {
+    const DistanceRange& r = p.ranges[n - 1 - k];  // ranges ascend in d
+    XZZX_CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->fork, 0));
+    if ((st = launch_chunks(r.d, anneal_launch(d, b->keys, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin),
+                            b->side[k])))
+      return st;
+    XZZX_CUDA_TRY(cudaEventRecord(b->done[k], b->side[k]));
+    XZZX_CUDA_TRY(cudaStreamWaitEvent(stream, b->done[k], 0));
+  }
+  return run_reduce(p, d, 0, p.total_shots, stream);
+}
+
+xzzx_status run_mode(xzzx_batch* b, int mode, cudaStream_t stream) {
+  if (mode == 3) return launch_concurrent(b, stream);
+  return xzzx::batch::launch_plan(b->plan, b->dev, b->keys, b->grid, mode, stream);
+}
+
 }  // namespace
 
 using namespace xzzx;
@@ -427,17 +472,24 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
   if (per_sm < 1) per_sm = 1;
   if (cfg && cfg->ctas_per_sm > 0) per_sm = std::min(per_sm, cfg->ctas_per_sm);
   b->grid = n_sm * per_sm;
+  b->graph_mode = cfg ? cfg->graph_mode : 0;
+  if (b->graph_mode != 0 && b->graph_mode != 3) {
+    free_batch(b);
+    return fail(XZZX_EINVAL, "graph_mode must be 0 or 3");
+  }
   *out = b;
   return XZZX_OK;
 }
 
 xzzx_status xzzx_batch_run(xzzx_batch* b, int mode, void* stream) {
   if (!b) return fail(XZZX_EINVAL, "batch is NULL");
-  if (mode < 0 || mode > 2)
-    return fail(XZZX_EINVAL, "mode must be 0 (batched), 1 (one launch per distance) or 2 (one warp per chain)");
+  if (mode < 0 || mode > 3)
+    return fail(XZZX_EINVAL,
+                "mode must be 0 (batched), 1 (one launch per distance), 2 (one warp per chain) or 3 (concurrent "
+                "per-distance launches)");
   xzzx_status st = check_device(b->device);
   if (st) return st;
-  return launch_plan(b->plan, b->dev, b->keys, b->grid, mode, (cudaStream_t)stream);
+  return run_mode(b, mode, (cudaStream_t)stream);
 }
 
 xzzx_status xzzx_batch_run_graph(xzzx_batch* b, void* stream) {
@@ -448,7 +500,7 @@ xzzx_status xzzx_batch_run_graph(xzzx_batch* b, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (!b->graph_exec) {
     XZZX_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    st = launch_plan(b->plan, b->dev, b->keys, b->grid, 0, s);
+    st = run_mode(b, b->graph_mode, s);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(s, &g);
     if (st) {

@@ -72,7 +72,7 @@ def test_batch_modes_match_per_segment_calls(env):
     info = b.info()
     assert info["n_segments"] == len(SEG_SPECS) and info["n_distances"] == 7
     assert info["launches_batched"] == 3 and info["launches_plain"] == 21
-    for mode in (0, 1, 2, 0):         # a second mode-0 run reuses the reset queue
+    for mode in (0, 1, 2, 3, 0, 3):   # second runs reuse the reset queue and the side streams
         for o in b.outputs:
             for t in o.values():
                 if t is not None:
@@ -88,6 +88,28 @@ def test_batch_modes_match_per_segment_calls(env):
             b.run_graph(s)
         s.synchronize()
         assert_same(b.outputs, refs)
+
+
+def test_batch_concurrent_mode_graph(env):
+    """Mode 3 (each distance's own launch on forked streams) captured as a
+    CUDA graph and replayed: identical outputs to the per-segment calls."""
+    X, torch = env
+    seed = 0x3C0C
+    segs = make_segments(X, torch, seed)
+    refs = reference_outputs(X, torch, segs, seed)
+    b = X.Batch(segs, seed, graph_mode=3)
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        for o in b.outputs:
+            for t in o.values():
+                if t is not None:
+                    t.fill_(0x3C)
+        with torch.cuda.stream(s):
+            b.run_graph(s)
+        s.synchronize()
+        assert_same(b.outputs, refs)
+    with pytest.raises(X.XzzxError):
+        X.Batch(segs, seed, graph_mode=1)
 
 
 def test_batch_small_segments_match_oracle(env):
