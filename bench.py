@@ -429,6 +429,24 @@ def run_large(args):
     att = shots * 4 * R * N * (d * d - 1) / (ms / 1e3)
     props = torch.cuda.get_device_properties(0)
     peak = props.multi_processor_count * 4 * 32 * 2070e6 / 1e12
+
+    # The same annealing launch (first p, step 1) with one warp per chain and
+    # colour-parallel lanes, against one thread per chain: identical chain
+    # minima, and each mapping's rate.
+    noise, sched, sd, err, syn = cases[0]
+    init, _ = X.greedy_init(code, noise, sd, S, syn[S:2 * S], R)
+    mapping = {}
+    best = {}
+    for name, per_warp in (("thread_per_chain", False), ("warp_per_chain", True)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        a = X.anneal(code, sched, sd, S, init, want_cfg=False, per_warp=per_warp, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        best[name] = a["best_E"]
+        mapping[name] = {"anneal_ms": e0.elapsed_time(e1),
+                         "attempts_per_s": S * 4 * R * N * (d * d - 1) / (e0.elapsed_time(e1) / 1e3)}
+    mapping["identical_chain_minima"] = bool(torch.equal(best["thread_per_chain"], best["warp_per_chain"]))
     print(json.dumps({
         "metric": "move-attempts/s and decoded shots/s at d=31 (256 restarts, 1e4 sweeps)",
         "value": att, "unit": "move-attempts/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
@@ -438,6 +456,7 @@ def run_large(args):
                                "1e4 sweeps, linear beta 0.02->30, scale 4096", "shots_per_p_per_step": S},
         "shots_per_s": shots / (ms / 1e3), "shots_timed": shots * args.steps,
         "logical_error_rates": [stats.ler_record(p, f, S * args.steps) for p, f in zip(LARGE_PS, fails)],
+        "chain_mapping": mapping,
         "roofline": {"bound": "alu", "achieved": att * I_ALG / 1e12, "peak": peak, "unit": "Tinst/s",
                      "frac": att * I_ALG / 1e12 / peak, "traffic": None,
                      "peak_basis": "152 SMs x 128 lanes x 2070 MHz"}}))
