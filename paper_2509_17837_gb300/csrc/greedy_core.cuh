@@ -276,45 +276,59 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
     const int nd = S.n_def[colour];
     const int nv = nd + (nd & 1);  // vertex nd is the virtual boundary vertex when nd is odd
     const int16_t* D = S.defects[colour];
-    for (int x = lane; x < nv; x += 32) partner[x] = -1;
+    for (int x = lane; x < nv; x += 32) {
+      partner[x] = -1;
+      best[x] = -1;
+    }
     __syncwarp();
     int unmatched = nv;
     while (unmatched > 0) {
-      // Each free vertex finds its best free partner in the order (w, key, u, v).
+      // Each free vertex finds its best free partner in the order (w, key, u, v),
+      // in one pass: a candidate's key is drawn only when its weight ties the
+      // best so far.  A best partner that is still free stays the best (removing
+      // other vertices cannot put one ahead of it), so only vertices whose best
+      // was matched in the last round search again.
       for (int x = lane; x < nv; x += 32) {
         if (partner[x] >= 0) {
           best[x] = -1;
           continue;
         }
+        const int bx = best[x];
+        if (bx >= 0 && partner[bx] < 0) continue;
         const bool xb = x == nd;
         const int fx = xb ? 0 : D[x];
-        int32_t wmin = kInf;
-        for (int y = 0; y < nv; ++y) {
-          if (y == x || partner[y] >= 0) continue;
-          int32_t wxy;
-          if (xb) wxy = S.wb[D[y]];
-          else if (y == nd) wxy = S.wb[fx];
-          else wxy = min(X.w_int(fx, D[y]), S.wb[fx] + S.wb[D[y]]);
-          wmin = min(wmin, wxy);
-        }
+        const uint32_t sx = xb ? kBoundary : (uint32_t)fx;
         int bestv = -1;
+        int32_t bw = kInf;
         uint32_t bkey = 0, bu = 0, bvv = 0;
+        bool bkey_ok = false;
         for (int y = 0; y < nv; ++y) {
           if (y == x || partner[y] >= 0) continue;
           int32_t wxy;
           if (xb) wxy = S.wb[D[y]];
           else if (y == nd) wxy = S.wb[fx];
           else wxy = min(X.w_int(fx, D[y]), S.wb[fx] + S.wb[D[y]]);
-          if (wxy != wmin) continue;
-          const uint32_t sx = xb ? kBoundary : (uint32_t)fx;
+          if (wxy > bw) continue;
           const uint32_t sy = (y == nd) ? kBoundary : (uint32_t)D[y];
           const uint32_t u = min(sx, sy), v = max(sx, sy);
+          if (wxy < bw) {
+            bestv = y;
+            bw = wxy;
+            bu = u;
+            bvv = v;
+            bkey_ok = false;
+            continue;
+          }
           uint32_t key = 0;
-          if (mode == kInitGreedyRandom)
-            key = philox4x32_10(u | (v << 16), (uint32_t)i, (uint32_t)shot, kTagGreedy | ((uint32_t)(shot >> 32) << 8),
-                                K).x;
-          const bool better = bestv < 0 || key < bkey || (key == bkey && (u < bu || (u == bu && v < bvv)));
-          if (better) {
+          if (mode == kInitGreedyRandom) {
+            const uint32_t c3 = kTagGreedy | ((uint32_t)(shot >> 32) << 8);
+            if (!bkey_ok) {
+              bkey = philox4x32_10(bu | (bvv << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
+              bkey_ok = true;
+            }
+            key = philox4x32_10(u | (v << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
+          }
+          if (key < bkey || (key == bkey && (u < bu || (u == bu && v < bvv)))) {
             bestv = y;
             bkey = key;
             bu = u;
