@@ -8,6 +8,7 @@ import re
 import numpy as np
 import pytest
 
+import golden_data
 import oracle as O
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -95,6 +96,14 @@ def test_weights_match_oracle(X, p, eta, conv, scale):
     assert (n.px, n.py, n.pz) == pxyz
     W4, Wt = O.make_noise(*pxyz, scale)
     assert list(n.W) == list(W4) and [n.Wt_x, n.Wt_z] == list(Wt)
+
+
+@pytest.mark.parametrize("p,eta,scale,wx,wy,wt", golden_data.weight_table())
+def test_library_weights_equal_printed_table(X, p, eta, scale, wx, wy, wt):
+    """xzzx_noise_from_eta gives the stored integer weights of Eqs. coeff_in_energy
+    and coeff_in_distance."""
+    n = X.noise_from_eta(p, eta, 0, scale)
+    assert list(n.W) == [0, wx, wx, wy] and [n.Wt_x, n.Wt_z] == [wt, wt]
 
 
 def reachable_positive_dE(W4):

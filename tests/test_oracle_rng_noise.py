@@ -16,19 +16,28 @@ import numpy as np
 import pytest
 
 import oracle as O
+import golden_data
 from inputs import random_paulis
 
-KAT = [  # (key, counter, output) for Philox4x32 with 10 rounds
-    (0x0000000000000000, [0, 0, 0, 0], [0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8]),
-    (0xFFFFFFFFFFFFFFFF, [0xFFFFFFFF] * 4, [0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD]),
-    (0x299F31D0A4093822, [0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344],
-     [0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1]),
-]
+KAT = golden_data.philox_kat()
 
 
 @pytest.mark.parametrize("key,ctr,out", KAT)
 def test_philox_known_answers(key, ctr, out):
     assert [int(x) for x in O.philox(key, ctr)] == out
+
+
+def test_kat_fixture_complete():
+    assert len(KAT) == 3
+
+
+@pytest.mark.parametrize("p,eta,scale,wx,wy,wt", golden_data.weight_table())
+def test_weights_equal_printed_table(p, eta, scale, wx, wy, wt):
+    """The oracle's integer weights equal the stored values of Eq. coeff_in_energy
+    (W_X = W_Z, W_Y) and Eq. coeff_in_distance (matching weights)."""
+    W4, Wt = O.make_noise(*O.noise_from_eta(p, eta), scale)
+    assert [int(x) for x in W4] == [0, wx, wx, wy]       # labels I, Z, X, Y
+    assert [int(x) for x in Wt] == [wt, wt]
 
 
 def test_philox_uniform():
