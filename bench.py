@@ -41,6 +41,12 @@ ANNEAL_DRAM_BYTES_PER_CHAIN = 1.4738e6 / 128000
 # sm__inst_executed_pipe_alu of the same capture x 32 / attempts); the ALU
 # pipe takes 16 lanes per clock per SM sub-partition.
 ANNEAL_ALU_INST_PER_ATTEMPT = 15.3
+# Counters of the same capture, per move attempt: lane instructions issued
+# (smsp__inst_executed x 32), and shared-memory bank conflicts per shared
+# wavefront.
+ANNEAL_MEASURED = {"inst_per_attempt": 25.5, "alu_inst_per_attempt": ANNEAL_ALU_INST_PER_ATTEMPT,
+                   "shared_bank_conflicts_per_wavefront": 1.45e9 / 2.59e9,
+                   "source": "ncu capture of one anneal_kernel<11> launch, profiles/anneal_d11_ncu_full.md"}
 
 
 def workload_config(shots_per_p, world):
@@ -81,11 +87,17 @@ def sum_over_ranks(values, dist, device):
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while the timed
+    region runs (written to ``path``, a temporary file unless one is given)."""
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, path, gpu_index):
+        if not path:
+            import tempfile
+            fd, path = tempfile.mkstemp(prefix="xzzx_clocks_", suffix=".csv")
+            os.close(fd)
         self.path, self.gpu_index, self.proc = path, gpu_index, None
 
     def start(self):
@@ -127,6 +139,27 @@ class ClockSampler:
         loaded = [x for x in sm if x >= 0.5 * top] or sm
         return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
                 "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def issue_peak(clocks, n_sm):
+    """Integer issue peak in T lane-instructions/s (SMs x 4 SMSP x 32 lanes x
+    the median SM clock sampled in the timed region), with its basis; (None,
+    reason) when no clock was sampled, so the roofline is reported unmeasured
+    rather than guessed."""
+    f_mhz = (clocks or {}).get("sm_mhz")
+    if not f_mhz:
+        return None, "unmeasured: no SM clock samples (%s)" % ",".join((clocks or {}).get("reasons", []) or ["none"])
+    return (n_sm * 4 * 32 * f_mhz * 1e6 / 1e12,
+            "%d SMs x 4 SMSP x 32 lanes x %.0f MHz (median SM clock sampled in the timed region)" % (n_sm, f_mhz))
+
+
+def roofline_record(rate_attempts, clocks, n_sm, **extra):
+    peak, basis = issue_peak(clocks, n_sm)
+    achieved = rate_attempts * I_ALG / 1e12
+    rec = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
+           "frac": (achieved / peak) if peak else None, "I_alg_per_attempt": I_ALG, "peak_basis": basis}
+    rec.update(extra)
+    return rec
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -185,6 +218,79 @@ def cpu_baseline_all_cores(shots_per_core):
     return {"value": attempts_per_shot() * done / dt, "unit": "move-attempts/s", "cores": n, "kind": "oracle",
             "sample": "%d processes x %d shots of d=11 p=0.16, %.1f s wall" % (n, shots_per_core, dt),
             "shots_per_s": done / dt}
+
+
+def _parity_worker(task):
+    """Oracle decode of listed d=11 shots of one noise point, shot by shot."""
+    pi, shots = task
+    import numpy as np
+    import oracle as O
+    pxyz = O.noise_from_eta(PS[pi], ETA)
+    out = {k: [] for k in ("cls", "E4", "recovery", "fail")}
+    for s in shots:
+        err, syn = O.sample(D, pxyz, SEED + pi, int(s), 1)
+        r = O.decode(D, pxyz, SCALE, O.LINEAR, SWEEPS, BETA0, BETA1, SEED + pi, int(s), RESTARTS, syn, err)
+        for k in out:
+            out[k].append(r[k][0])
+    return pi, list(shots), {k: np.array(v) for k, v in out.items()}
+
+
+class ParityLeg:
+    """Oracle parity on a seeded sample of the shots of the last timed step.
+
+    The oracle decodes the sampled shots in spawned single-threaded processes
+    on all host cores but one while the GPU runs; afterwards each shot's
+    class, coset energies, recovery and failure flag are compared with the
+    GPU's outputs element by element."""
+
+    def __init__(self, shot_first, S, per_p, seed=0x9A7):
+        import numpy as np
+        self.picks = [np.sort(np.random.default_rng(seed + pi).choice(S, min(per_p, S), replace=False))
+                      for pi in range(len(PS))]
+        self.shot_first, self.per_p = shot_first, per_p
+        self.pool = self.result = None
+        if per_p <= 0:
+            return
+        import multiprocessing as mp
+        import oracle.build
+        oracle.build.build()
+        n = max(1, (os.cpu_count() or 2) - 1)
+        tasks = []
+        for pi, pk in enumerate(self.picks):
+            shots = (shot_first[pi] + pk).tolist()
+            step = max(1, (len(PS) * per_p) // (3 * n))
+            tasks += [(pi, shots[j:j + step]) for j in range(0, len(shots), step)]
+        self.cores = n
+        self.t0 = time.perf_counter()
+        self.pool = mp.get_context("spawn").Pool(n)
+        self.result = self.pool.map_async(_parity_worker, tasks, chunksize=1)
+
+    def compare(self, gpu_outs, words):
+        """gpu_outs[pi]: dict of the last step's device outputs for noise point pi."""
+        if self.pool is None:
+            return None
+        import numpy as np
+        parts = self.result.get()
+        wall = time.perf_counter() - self.t0
+        self.pool.close()
+        self.pool.join()
+        host = [{k: v.cpu().numpy() for k, v in o.items() if v is not None} for o in gpu_outs]
+        mism, shots, bad = 0, 0, []
+        for pi, shot_ids, ref in parts:
+            g = host[pi]
+            rows = [int(s) - self.shot_first[pi] for s in shot_ids]
+            rec = g["recovery"][rows].view(np.uint32)
+            x = np.unpackbits(rec[:, :words].view(np.uint8), axis=1, bitorder="little")[:, :D * D]
+            z = np.unpackbits(rec[:, words:].view(np.uint8), axis=1, bitorder="little")[:, :D * D]
+            lab = (x << 1) | z
+            ok = ((g["cls"][rows] == ref["cls"]) & (g["E4"][rows] == ref["E4"]).all(1) &
+                  (lab == ref["recovery"]).all(1) & (g["fail"][rows] == ref["fail"]))
+            shots += len(rows)
+            mism += int((~ok).sum())
+            bad += [int(s) for s, o in zip(shot_ids, ok) if not o][:4]
+        return {"shots": shots, "mismatches": mism, "compared": "cls, E4 (4 coset minima), recovery, fail",
+                "source": "seeded sample of the last timed step's shots, %d per p" % self.per_p,
+                "oracle_processes": self.cores, "oracle_wall_s": wall, "first_mismatched_shots": bad}
 
 
 def cpu_baseline(shots):
@@ -276,18 +382,20 @@ def run_uneven(args):
         return ms / steps
 
     conc = X.Batch(segs, seed, graph_mode=3)
+    sampler = ClockSampler(args.clocks_csv, dev)
+    sampler.start()
     with torch.cuda.stream(stream):
         ms_batched = timed(lambda: batch.run_graph(stream), args.steps, args.warmup)
         out_b = [{k: (v.clone() if v is not None else None) for k, v in o.items()} for o in batch.outputs]
         ms_plain = timed(lambda: batch.run(1, stream), args.steps, 1)
         ms_conc = timed(lambda: conc.run_graph(stream), args.steps, 1)
     stream.synchronize()
+    clocks = sampler.stop()
     same = all(torch.equal(a[k], b[k]) for a, b in zip(out_b, batch.outputs) for k in a if a[k] is not None)
     same = same and all(torch.equal(a[k], b[k]) for a, b in zip(out_b, conc.outputs) for k in a if a[k] is not None)
     fails = sum(int(o["fail"].sum()) for o in batch.outputs)
     shots = info["total_shots"]
     props = torch.cuda.get_device_properties(dev)
-    peak = props.multi_processor_count * 4 * 32 * 2070e6 / 1e12
     att = info["move_attempts"] / (ms_batched / 1e3)
     print(json.dumps({
         "metric": "decoded shots/s, uneven batch (d in {5,7,9,13,17,21}, persistent launch vs one launch per distance)",
@@ -311,10 +419,9 @@ def run_uneven(args):
                              "speedup_vs_plain": ms_plain / ms_conc,
                              "form": "each distance's own kernel on forked streams, captured as one graph"},
         "launches": {"batched_graph": info["launches_batched"], "plain": info["launches_plain"]},
-        "logical_failures": fails,
-        "roofline": {"bound": "alu", "achieved": att * I_ALG / 1e12, "peak": peak, "unit": "Tinst/s",
-                     "frac": att * I_ALG / 1e12 / peak, "traffic": None,
-                     "peak_basis": "152 SMs x 128 lanes x 2070 MHz"}}))
+        "logical_failures": fails, "clocks": clocks,
+        "roofline": roofline_record(att, clocks, props.multi_processor_count, traffic=None,
+                                    kernel="persistent annealing launch (all distances)")}))
 
 
 # --------------------------------------------------------------------------- serving (NEXT f2)
@@ -424,11 +531,13 @@ def run_large(args):
 
     step(0)
     fails = [0] * len(cases)
+    sampler = ClockSampler(args.clocks_csv, torch.cuda.current_device())
+    sampler.start()
     ms = sum(step(k + 1) for k in range(args.steps)) / args.steps
+    clocks = sampler.stop()
     shots = S * len(LARGE_PS)
     att = shots * 4 * R * N * (d * d - 1) / (ms / 1e3)
     props = torch.cuda.get_device_properties(0)
-    peak = props.multi_processor_count * 4 * 32 * 2070e6 / 1e12
 
     # The same annealing launch (first p, step 1) with one warp per chain and
     # colour-parallel lanes, against one thread per chain: identical chain
@@ -456,10 +565,9 @@ def run_large(args):
                                "1e4 sweeps, linear beta 0.02->30, scale 4096", "shots_per_p_per_step": S},
         "shots_per_s": shots / (ms / 1e3), "shots_timed": shots * args.steps,
         "logical_error_rates": [stats.ler_record(p, f, S * args.steps) for p, f in zip(LARGE_PS, fails)],
-        "chain_mapping": mapping,
-        "roofline": {"bound": "alu", "achieved": att * I_ALG / 1e12, "peak": peak, "unit": "Tinst/s",
-                     "frac": att * I_ALG / 1e12 / peak, "traffic": None,
-                     "peak_basis": "152 SMs x 128 lanes x 2070 MHz"}}))
+        "chain_mapping": mapping, "clocks": clocks,
+        "roofline": roofline_record(att, clocks, props.multi_processor_count, traffic=None,
+                                    kernel="anneal_kernel<31>")}))
 
 
 # --------------------------------------------------------------------------- logical error rate curves
@@ -550,6 +658,9 @@ def main():
     ap.add_argument("--cpu-shots-per-core", type=int, default=16)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-greedy-only", action="store_true")
+    ap.add_argument("--parity-shots-per-p", type=int, default=100)
+    ap.add_argument("--clocks-csv", default=None, help="where to keep the nvidia-smi clock samples")
     ap.add_argument("--workload", default="d11", choices=["d11", "uneven", "serve", "large", "ler"])
     ap.add_argument("--ler-shots", type=int, default=100000)
     ap.add_argument("--layout", default="rotated", choices=["rotated", "planar"])
@@ -637,14 +748,18 @@ def main():
             res = X.decode_reduce(code, init, cbits, chain_E, true_errors=err, stream=stream)
             e[3].record(stream)
             o["fail"] = res["fail"]
+            o["res"] = res
             times.append(e)
         return times
 
+    # oracle parity on a sample of the last timed step's shots, computed on the
+    # host cores while the GPU runs (rank 0)
+    parity = ParityLeg([c["shot_base"] + (n_steps - 1) * S for c in cases], S,
+                       args.parity_shots_per_p if rank == 0 else 0)
     for k in range(args.warmup):
         step(k, False)
     barrier()
-    sampler = ClockSampler(os.path.join(ROOT, "gpurun_out", "bench_clocks.csv") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/bench_clocks_%d.csv" % os.getpid(), dev)
+    sampler = ClockSampler(args.clocks_csv, dev)
     if rank == 0:
         sampler.start()
         time.sleep(0.5)
@@ -682,12 +797,19 @@ def main():
     anneal_rate = S * attempts_per_shot() / (anneal_ms_per_launch / 1e3)  # per GPU
 
     result = None
+    last_outs = [o["res"] for o in outs]
     if rank == 0:
         props = torch.cuda.get_device_properties(dev)
         n_sm = props.multi_processor_count
-        f_mhz = clocks.get("sm_mhz") or 1920.0
-        peak = n_sm * 4 * 32 * f_mhz * 1e6 / 1e12  # T lane-instructions/s
-        achieved = anneal_rate * I_ALG / 1e12
+        f_mhz = (clocks or {}).get("sm_mhz")
+        roof = roofline_record(
+            anneal_rate, clocks, n_sm, traffic=ANNEAL_DRAM_BYTES_PER_CHAIN * S * RESTARTS * 4,
+            kernel="anneal_kernel<11>",
+            measured_per_attempt=ANNEAL_MEASURED,
+            secondary_alu_pipe=None if not f_mhz else {
+                "alu_inst_per_attempt": ANNEAL_ALU_INST_PER_ATTEMPT,
+                "peak_attempts_per_s": n_sm * 4 * 16 * f_mhz * 1e6 / ANNEAL_ALU_INST_PER_ATTEMPT,
+                "frac": anneal_rate / (n_sm * 4 * 16 * f_mhz * 1e6 / ANNEAL_ALU_INST_PER_ATTEMPT)})
         result = {
             "metric": "move-attempts/s and decoded shots/s at d=11 (64 restarts); serve p50/p99 latency",
             "value": value, "unit": "move-attempts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -698,55 +820,78 @@ def main():
             "anneal_attempts_per_s_per_gpu": anneal_rate,
             "kernel_ms_per_step": {"greedy": g_ms / args.steps, "anneal": a_ms / args.steps,
                                    "reduce": r_ms / args.steps},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tinst/s",
-                         "frac": achieved / peak, "traffic": ANNEAL_DRAM_BYTES_PER_CHAIN * S * RESTARTS * 4,
-                         "kernel": "anneal_kernel<11>", "I_alg_per_attempt": I_ALG,
-                         "peak_basis": "%d SMs x 4 SMSP x 32 lanes x %.0f MHz (median SM clock sampled in the timed region)"
-                                       % (n_sm, f_mhz),
-                         "secondary_alu_pipe": {
-                             "alu_inst_per_attempt": ANNEAL_ALU_INST_PER_ATTEMPT,
-                             "peak_attempts_per_s": n_sm * 4 * 16 * f_mhz * 1e6 / ANNEAL_ALU_INST_PER_ATTEMPT,
-                             "frac": anneal_rate / (n_sm * 4 * 16 * f_mhz * 1e6 / ANNEAL_ALU_INST_PER_ATTEMPT)}},
+            "roofline": roof,
             "clocks": clocks, "gpu_launches": 3 * len(PS) * args.steps,
             "logical_error_rates": [stats.ler_record(p, f, S * args.steps * world) for p, f in zip(PS, fail_dev)],
             "wall_s_timed_region": wall,
         }
+    # ---------------------------------------------------------------- greedy-only decisions (0 sweeps)
+    # The same shots decided from the 256 initial configurations R_i L_P alone
+    # (no annealing): the logical error rate SA improves on.
+    if not args.no_greedy_only:
+        fails0 = [0] * len(PS)
+        for ci, c in enumerate(cases):
+            sched0 = X.Schedule(c["noise"], 0, BETA0, BETA1)
+            for k in range(args.warmup, n_steps):
+                s0 = k * S
+                X.greedy_init(code, c["noise"], c["seed"], c["shot_base"] + s0, c["syn"][s0:s0 + S], RESTARTS,
+                              init=init, cbits=cbits, stream=stream)
+                X.anneal(code, sched0, c["seed"], c["shot_base"] + s0, init, want_cfg=False, best_E=chain_E,
+                         stream=stream)
+                r0 = X.decode_reduce(code, init, cbits, chain_E, true_errors=c["err"][s0:s0 + S], stream=stream)
+                fails0[ci] += int(r0["fail"].sum())
+        if world > 1:
+            fails0 = [int(f) for f in sum_over_ranks([float(f) for f in fails0], dist, dev)]
+        if rank == 0:
+            result["logical_error_rates_greedy_only"] = [stats.ler_record(p, f, S * args.steps * world)
+                                                         for p, f in zip(PS, fails0)]
+    # ---------------------------------------------------------------- oracle parity (rank 0)
+    if rank == 0 and parity.pool is not None:
+        result["parity"] = parity.compare(last_outs, code.words)
     # ---------------------------------------------------------------- e2e through the C ABI, host buffers
+    # Every step copies its own shots' syndromes and true errors in from
+    # pinned host memory, decodes them with xzzx_decode_batch, and copies the
+    # classes and failure flags out; steps take fresh shots.
     if not args.no_e2e:
         c = cases[2]
-        syn_h = c["syn"][:S].cpu().pin_memory()
-        err_h = c["err"][:S].cpu().pin_memory()
+        syn_h = c["syn"].cpu().pin_memory()
+        err_h = c["err"].cpu().pin_memory()
         syn_d = torch.empty_like(c["syn"][:S])
         err_d = torch.empty_like(c["err"][:S])
         cls_h = torch.empty(S, dtype=torch.uint8).pin_memory()
         fail_h = torch.empty(S, dtype=torch.uint8).pin_memory()
         ws = torch.empty(X.decode_workspace_size(code, S, RESTARTS), dtype=torch.uint8, device=dev)
-        o = outs[2]
+        o = {k: v for k, v in outs[2]["res"].items()}
 
         def e2e_step(k):
-            syn_d.copy_(syn_h, non_blocking=True)
-            err_d.copy_(err_h, non_blocking=True)
-            X.decode_batch(code, c["noise"], c["sched"], c["seed"], c["shot_base"] + k * S, syn_d, RESTARTS,
+            s0 = (k % n_steps) * S
+            syn_d.copy_(syn_h[s0:s0 + S], non_blocking=True)
+            err_d.copy_(err_h[s0:s0 + S], non_blocking=True)
+            X.decode_batch(code, c["noise"], c["sched"], c["seed"], c["shot_base"] + s0, syn_d, RESTARTS,
                            true_errors=err_d, out=o, workspace=ws, stream=stream)
             cls_h.copy_(o["cls"], non_blocking=True)
             fail_h.copy_(o["fail"], non_blocking=True)
             torch.cuda.current_stream().synchronize()
 
-        e2e_step(0)
-        barrier()
-        t0 = time.perf_counter()
-        n_e2e = 2
-        for k in range(n_e2e):
+        for k in range(min(args.warmup, 1)):
             e2e_step(k)
         barrier()
+        t0 = time.perf_counter()
+        n_e2e = args.steps
+        for k in range(n_e2e):
+            e2e_step(args.warmup + k)
+        barrier()
         e2e_s = (time.perf_counter() - t0) / n_e2e
+        if world > 1:
+            e2e_s = max_over_ranks([e2e_s], dist, dev)[0]
         if rank == 0:
             result["e2e"] = {"value": S * attempts_per_shot() * world / e2e_s, "unit": "move-attempts/s",
-                             "h2d_bytes_per_step": syn_h.numel() * 4 + err_h.numel() * 4,
+                             "h2d_bytes_per_step": S * (syn_h.shape[1] + err_h.shape[1]) * 4,
                              "d2h_bytes_per_step": cls_h.numel() + fail_h.numel(),
-                             "shots_per_s": S * world / e2e_s,
-                             "note": "one batch of %d shots at p=0.16 per step through xzzx_decode_batch; pinned "
-                                     "host syndromes/errors copied in, classes and failure flags copied out" % S}
+                             "shots_per_s": S * world / e2e_s, "steps": n_e2e,
+                             "note": "per step one batch of %d fresh shots at p=0.16 through xzzx_decode_batch: "
+                                     "pinned host syndromes and true errors copied in, classes and failure "
+                                     "flags copied out, stream synchronised" % S}
     if rank == 0 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args.cpu_shots)
         result["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.cpu_shots_per_core)

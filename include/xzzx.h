@@ -62,6 +62,16 @@ typedef enum {
 /* Message describing the last failure on the calling thread ("" if none). */
 const char* xzzx_last_error(void);
 
+/* Device-side error flags.  Kernels never trap: a failure they detect is
+ * recorded in the error area of the code handle the work used and the work
+ * goes on.  XZZX_DEVERR_GREEDY_WALK: a greedy path walk or matching round
+ * could not complete (never expected on a valid code; that reference then
+ * does not reproduce its syndrome, and bit 7 of its cbits byte is set).
+ * XZZX_DEVERR_BOUNDS: a bounds check of the checked build (compiled with
+ * -DXZZX_CHECKS) found an index outside its buffer and skipped the access. */
+#define XZZX_DEVERR_GREEDY_WALK 0x1u
+#define XZZX_DEVERR_BOUNDS 0x2u
+
 /* Library version string. */
 const char* xzzx_version(void);
 
@@ -93,6 +103,23 @@ typedef struct {
 xzzx_status xzzx_make_code(int d, int layout, xzzx_code** out);
 xzzx_status xzzx_get_code_info(const xzzx_code* code, xzzx_code_info* out);
 void xzzx_free_code(xzzx_code* code);
+
+/* Read the device-side error flags raised by work done with this code (OR
+ * of XZZX_DEVERR_*) into *flags and how many times one was raised into
+ * *count (either may be NULL), after the work already queued on stream;
+ * with clear != 0 they are reset to zero after the read.  Synchronises
+ * stream.  Work on other streams is included once it has finished. */
+xzzx_status xzzx_device_errors(const xzzx_code* code, uint32_t* flags, uint32_t* count, int clear, void* stream);
+
+/* Test hook: ask the kernels that use this code to raise the given
+ * XZZX_DEVERR_* flags as if the failure had happened, without faulting
+ * anything (flags = 0 turns it off).  GREEDY_WALK marks restart 0 of every
+ * shot in xzzx_greedy_init (bit 7 of its cbits byte; the reference itself is
+ * unchanged); in the checked build, BOUNDS makes the bounds check of the
+ * annealing kernels' table lookup fail, which skips the lookup (the move is
+ * then taken with dE = 0, so energies are no longer meaningful) and raises
+ * the flag.  The plain build ignores BOUNDS.  Ordered on stream. */
+xzzx_status xzzx_debug_inject(const xzzx_code* code, uint32_t flags, void* stream);
 
 /* Generator f as four corner qubits (-1 outside) in the order of its X, Z, Z,
  * X factors (rotated TL, TR, BL, BR; planar left, up, down, right) and its
@@ -344,6 +371,7 @@ typedef struct {
 typedef struct {
   int64_t submitted, rejected, dispatched, completed, batches, pending, in_flight;
   double mean_batch, p50_us, p99_us, max_us, mean_us;
+  uint32_t device_errors;  /* OR of the XZZX_DEVERR_* flags raised by any batch since start */
 } xzzx_serve_stats;
 
 typedef struct xzzx_server xzzx_server;
@@ -396,7 +424,12 @@ void xzzx_serve_destroy(xzzx_server* s);
  * to start at zero (each call writes what it reads).  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress, once
  * per device, that device current); make that first call before any stream
- * capture. */
+ * capture.  Under lazy module loading (the CUDA default) that first call is
+ * also when the array's 16 MiB are committed on the device, so a caller that
+ * must not allocate later makes a warm-up call with n_shots = 0 at start-up
+ * (it only does this set-up).  The cached address does not survive a
+ * cudaDeviceReset of the device; do not call this entry point on a device
+ * after resetting it. */
 xzzx_status xzzx_decode_batch_static(const xzzx_code* code, const xzzx_noise* noise, const xzzx_schedule* sched,
                                      uint64_t seed, uint64_t shot0, int n_shots, int restarts, int randomised,
                                      const uint32_t* syndromes, const uint32_t* true_errors, uint8_t* cls,

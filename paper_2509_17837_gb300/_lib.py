@@ -11,6 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libxzzx.so")
 
 XZZX_OK, XZZX_EINVAL, XZZX_ENOMEM, XZZX_ECUDA, XZZX_ETIMEOUT, XZZX_EBUSY, XZZX_EUNSUPPORTED = range(7)
+XZZX_DEVERR_GREEDY_WALK, XZZX_DEVERR_BOUNDS = 0x1, 0x2
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "ETIMEOUT", "EBUSY", "EUNSUPPORTED"]
 
 
@@ -65,7 +66,8 @@ class ServeStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("rejected", C.c_int64), ("dispatched", C.c_int64),
                 ("completed", C.c_int64), ("batches", C.c_int64), ("pending", C.c_int64),
                 ("in_flight", C.c_int64), ("mean_batch", C.c_double), ("p50_us", C.c_double),
-                ("p99_us", C.c_double), ("max_us", C.c_double), ("mean_us", C.c_double)]
+                ("p99_us", C.c_double), ("max_us", C.c_double), ("mean_us", C.c_double),
+                ("device_errors", C.c_uint32)]
 
 
 _p = C.c_void_p
@@ -75,6 +77,8 @@ _d = C.c_double
 
 SIGNATURES = {
     "xzzx_last_error": ([], C.c_char_p),
+    "xzzx_device_errors": ([_p, _p, _p, _i, _p], _i),
+    "xzzx_debug_inject": ([_p, C.c_uint32, _p], _i),
     "xzzx_version": ([], C.c_char_p),
     "xzzx_make_code": ([_i, _i, C.POINTER(_p)], _i),
     "xzzx_get_code_info": ([_p, C.POINTER(CodeInfo)], _i),

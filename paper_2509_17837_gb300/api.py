@@ -71,6 +71,17 @@ class Code:
              corners.ctypes.data_as(C.c_void_p))
         return a, b, corners
 
+    def device_errors(self, clear=False, stream=None):
+        """(flags, count) of the device-side errors raised by work done with
+        this code (XZZX_DEVERR_*); synchronises the stream."""
+        flags, count = C.c_uint32(), C.c_uint32()
+        call("xzzx_device_errors", self._h, C.byref(flags), C.byref(count), int(bool(clear)), _stream(stream))
+        return flags.value, count.value
+
+    def debug_inject(self, flags, stream=None):
+        """Test hook: make the kernels raise these XZZX_DEVERR_* flags."""
+        call("xzzx_debug_inject", self._h, flags, _stream(stream))
+
     def close(self):
         if self._h:
             lib().xzzx_free_code(self._h)

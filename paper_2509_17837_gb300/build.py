@@ -4,6 +4,11 @@ Each ``csrc/*.cu`` file is compiled in parallel into ``_build/`` and linked into
 ``libxzzx.so`` beside this file.  Host code is compiled with floating-point
 contraction off so that the FP64 threshold table rounds the same way on every
 host.
+
+``build(checks=True)`` builds the checked variant ``libxzzx_checks.so`` (in
+``_build_checks/``) with ``-DXZZX_CHECKS``: device-side bounds checks that
+record XZZX_DEVERR_BOUNDS in the code's error area and skip the access
+instead of trapping.  It exports the same C ABI.
 """
 import concurrent.futures as cf
 import glob
@@ -16,6 +21,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxzzx.so")
+BUILD_CHECKS = os.path.join(HERE, "_build_checks")
+LIB_CHECKS = os.path.join(HERE, "libxzzx_checks.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,22 +46,25 @@ def _deps():
         os.path.join(INCLUDE, "xzzx.h"), os.path.abspath(__file__)]
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+def up_to_date(lib=LIB):
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(p) <= t for p in _deps())
 
 
-def build(force=False, verbose_ptxas=False, jobs=None):
-    if not force and up_to_date():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose_ptxas=False, jobs=None, checks=False):
+    lib, bdir = (LIB_CHECKS, BUILD_CHECKS) if checks else (LIB, BUILD)
+    if not force and up_to_date(lib):
+        return lib
+    os.makedirs(bdir, exist_ok=True)
     cc = nvcc()
     extra = ["-Xptxas", "-v"] if verbose_ptxas else []
+    if checks:
+        extra.append("-DXZZX_CHECKS")
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         cmd = [cc, "-c", src, "-o", obj] + NVCC_FLAGS + extra
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -67,14 +77,14 @@ def build(force=False, verbose_ptxas=False, jobs=None):
     if verbose_ptxas:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-lcudart"]
+    tmp = lib + ".tmp.%d" % os.getpid()
+    cmd = [cc, "-shared", "-o", tmp] + [o for o, _ in results] + ARCH + ["-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, checks="--checks" in sys.argv))

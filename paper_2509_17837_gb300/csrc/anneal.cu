@@ -22,6 +22,7 @@ struct AnnealArgs {
   uint32_t* best_cfg;
   int32_t* final_E;
   uint32_t* final_cfg;
+  uint32_t* err;
 };
 
 template <int D>
@@ -38,6 +39,7 @@ __global__ void __launch_bounds__(Shape<D>::kThreads) anneal_kernel(const __grid
   tab.n_sweeps = A.n_sweeps;
   tab.n_classes = A.n_classes;
   for (int k = 0; k < 4; ++k) tab.W[k] = A.W[k];
+  tab.err = A.err;
   ChainOut out;
   out.best_E = A.best_E + c;
   out.best_cfg = A.best_cfg ? A.best_cfg + (size_t)c * 2 * W : nullptr;
@@ -73,6 +75,7 @@ xzzx_status launch_anneal_planar(const xzzx_code* code, const xzzx_schedule* sch
 xzzx_status launch_anneal(const xzzx_code* code, const xzzx_schedule* sched, uint64_t seed, uint64_t shot0,
                           int n_shots, int restarts, const uint32_t* init, int32_t* best_E, uint32_t* best_cfg,
                           int32_t* final_E, uint32_t* final_cfg, cudaStream_t stream) {
+  NvtxRange nvtx_range("xzzx K2 anneal");
   if (code->layout == kLayoutPlanar)  // colour sweep, minimum per colour phase
     return launch_anneal_planar(code, sched, seed, shot0, n_shots, restarts, 0, 0, init, best_E, best_cfg, final_E,
                                 final_cfg, stream);
@@ -91,6 +94,7 @@ xzzx_status launch_anneal(const xzzx_code* code, const xzzx_schedule* sched, uin
   A.best_cfg = best_cfg;
   A.final_E = final_E;
   A.final_cfg = final_cfg;
+  A.err = code->dev.err;
   switch (code->d) {
 #define XZZX_CASE(DD) \
   case DD:            \

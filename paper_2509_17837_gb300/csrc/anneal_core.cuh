@@ -158,7 +158,7 @@ __device__ __forceinline__ void store_rows(const Row (&R)[D], uint32_t* __restri
 // One colour phase of one sweep.
 template <int D, int C, typename Row>
 __device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint2* __restrict__ L, uint32_t t,
-                                             uint32_t c2, uint32_t c3, const PhiloxKeys& K) {
+                                             uint32_t c2, uint32_t c3, const PhiloxKeys& K, uint32_t* err) {
   // Rows of this colour: a = 2j + AOFF; colour 0 ends with the bottom boundary
   // row a = d-1, colour 3 starts with the top boundary row a = -1.
   constexpr int NR = (C == 0 || C == 3) ? (D + 1) / 2 : (D - 1) / 2;
@@ -189,7 +189,7 @@ __device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint
         const int a1 = a + 1 > D - 1 ? D - 1 : a + 1;
         idx = nib(R[a0], s) | (nib(R[a1], s) << 4);     // TL | TR << 2 | BL << 4 | BR << 6
       }
-      e[j] = L[idx];
+      e[j] = XZZX_CHECK(err, idx < (uint32_t)kLutN && !injected(err, XZZX_DEVERR_BOUNDS)) ? L[idx] : make_uint2(0u, 0u);
     }
     uint4 r[NG];
 #pragma unroll
@@ -239,7 +239,7 @@ __device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint
         idx = sig_base(kRight) + (((uint32_t)(R[a] >> sr) & 3u) | (((uint32_t)(R[a + 1] >> sr) & 3u) << 2));
       else  // TR | BR << 2
         idx = sig_base(kLeft) + (((uint32_t)R[a] & 3u) | (((uint32_t)R[a + 1] & 3u) << 2));
-      e[j] = L[idx];
+      e[j] = XZZX_CHECK(err, idx < (uint32_t)kLutN && !injected(err, XZZX_DEVERR_BOUNDS)) ? L[idx] : make_uint2(0u, 0u);
     }
     uint4 r[NG];
 #pragma unroll
@@ -290,6 +290,7 @@ struct SweepTables {
   const int2* sig;
   int n_sweeps, n_classes;
   int32_t W[4];
+  uint32_t* err;  // the code's device error area (bounds checks of the checked build)
 };
 
 // Output pointers of one chain (already offset to it), or null.
@@ -353,7 +354,7 @@ __device__ __forceinline__ void anneal_cta(const uint32_t* __restrict__ init, ui
   for (int t = 0; t < n_sweeps; ++t) {
     const uint32_t tt = (uint32_t)t;
 #define XZZX_PHASE(CC)                                                              \
-  colour_phase<D, CC, Row>(R, E, L, tt, c2, c3, K);                                 \
+  colour_phase<D, CC, Row>(R, E, L, tt, c2, c3, K, tab.err);                        \
   if (E < E_best) {                                                                 \
     E_best = E;                                                                     \
     _Pragma("unroll") for (int r = 0; r < D; ++r) best_rows[r * NT + tid] = R[r];   \

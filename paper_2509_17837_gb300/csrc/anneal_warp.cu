@@ -63,6 +63,7 @@ xzzx_status launch_anneal_warp(const xzzx_code* code, const xzzx_schedule* sched
   A.tab.n_sweeps = sched->n_sweeps;
   A.tab.n_classes = sched->n_classes;
   for (int k = 0; k < 4; ++k) A.tab.W[k] = sched->noise.W[k];
+  A.tab.err = code->dev.err;
   A.init = init;
   A.best_E = best_E;
   A.best_cfg = best_cfg;
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(kWPC * 32) warp_chains_kernel(const __grid_con
   tab.n_sweeps = sg.n_sweeps;
   tab.n_classes = sg.n_classes;
   for (int k = 0; k < 4; ++k) tab.W[k] = sg.W[k];
+  tab.err = sg.code.err;
   core::ChainOut out;
   out.best_E = sg.chain_E + c;
   out.best_cfg = nullptr;

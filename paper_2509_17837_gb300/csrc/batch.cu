@@ -314,6 +314,7 @@ xzzx_status configure_plan_kernels(int dmax, int* ctas_per_sm) {
 
 xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, int grid, int mode,
                         cudaStream_t stream) {
+  NvtxRange nvtx_range(mode == 0 ? "xzzx batch (persistent)" : "xzzx batch (per distance)");
   xzzx_status st;
   const int n_chunks = (int)p.lpt.size();
   if (mode == 0) {

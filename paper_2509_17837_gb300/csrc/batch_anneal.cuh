@@ -27,6 +27,7 @@ __device__ __forceinline__ void run_chunk(const ChunkDev& ch, const SegDev& sg, 
   tab.n_sweeps = ch.n_sweeps;
   tab.n_classes = ch.n_classes;
   for (int k = 0; k < 4; ++k) tab.W[k] = ch.W[k];
+  tab.err = sg.code.err;
   core::ChainOut out;
   out.best_E = sg.chain_E + c;
   out.best_cfg = nullptr;

@@ -65,6 +65,7 @@ xzzx_status launch_reduce(const xzzx_code* code, int n_shots, int restarts, cons
                           const int32_t* chain_E, const uint32_t* chain_cfg, const uint32_t* true_errors, uint8_t* cls,
                           int32_t* E4, uint32_t* recovery, uint32_t* best_cfg_out, uint8_t* fail_out,
                           cudaStream_t stream) {
+  NvtxRange nvtx_range("xzzx K3 reduce");
   ReduceArgs A;
   A.code = code->dev;
   A.n_shots = n_shots;
@@ -135,6 +136,7 @@ xzzx_status xzzx_decode_batch(const xzzx_code* code, const xzzx_noise* noise, co
   const Workspace L = layout(code, n_shots, restarts, best_cfg_out != nullptr);
   if (workspace_bytes < L.total)
     return fail(XZZX_EINVAL, "workspace too small: need " + std::to_string(L.total) + " bytes");
+  NvtxRange nvtx_range("xzzx decode_batch");
   char* ws = (char*)workspace;
   uint32_t* init = (uint32_t*)(ws + L.o_init);
   uint8_t* cbits = (uint8_t*)(ws + L.o_cbits);

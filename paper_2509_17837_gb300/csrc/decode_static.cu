@@ -21,7 +21,15 @@
 //    matter;
 //  * the first call on a device looks up the array's device address with
 //    cudaGetSymbolAddress (device current, once per device); make that first
-//    call before any stream capture.
+//    call before any stream capture.  With lazy module loading (the CUDA
+//    default) that lookup is also what loads this file's module on the
+//    device, so the 16 MiB are committed by the first call, not when the
+//    library is loaded.  A caller that must not allocate later makes one
+//    warm-up call with n_shots = 0 at start-up: it does the lookup and
+//    decodes nothing;
+//  * the address is cached per device index for the life of the process; a
+//    cudaDeviceReset of a device destroys the array it points to, so the
+//    entry point must not be used on that device after such a reset.
 #include <mutex>
 
 #include "internal.h"
@@ -29,7 +37,8 @@
 namespace xzzx {
 namespace {
 
-constexpr size_t kStaticScratchBytes = (size_t)16 << 20;
+constexpr size_t kStaticScratchBytes = XZZX_STATIC_SCRATCH_BYTES;
+static_assert(kStaticScratchBytes == ((size_t)16 << 20), "the header states 16 MiB");
 constexpr int kMaxDevices = 64;
 
 // The array's name is only a host-side stand-in for it; host code must pass

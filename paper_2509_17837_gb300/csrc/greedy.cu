@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(kWarps * 32) greedy_kernel(const __grid_consta
 xzzx_status launch_greedy(const xzzx_code* code, const xzzx_noise* noise, uint64_t seed, uint64_t shot0, int n_shots,
                           int restarts, int randomised, const uint32_t* syndromes, uint32_t* init, uint8_t* cbits,
                           cudaStream_t stream) {
+  NvtxRange nvtx_range("xzzx K1 greedy");
   GreedyArgs A;
   A.code = code->dev;
   A.keys = philox_keys(seed);

@@ -17,8 +17,9 @@
 // toward the target whenever one is needed and possible, else an X step; to
 // the boundary, the first of Z(+1,+1), Z(-1,-1), X(+1,-1), X(-1,+1) that lowers
 // the boundary distance by its weight), added modulo two into the warp's
-// configuration.  Bit 7 of cbits flags a walk that could not complete (never
-// expected on a valid code).
+// configuration.  A walk that could not complete (never expected on a valid
+// code) sets bit 7 of cbits and raises XZZX_DEVERR_GREEDY_WALK in the code's
+// error area.
 #pragma once
 
 #include "internal.h"
@@ -110,13 +111,17 @@ struct Ctx {
   const SharedT<G>& S;
   int d, w;
   int32_t Wt_x, Wt_z;
+  uint32_t* err;  // the code's device error area
+  int nq;
   __device__ int face(int a, int b) const { return G::face(S.at, d, a, b); }
   __device__ int qubit(int r, int c) const { return G::qubit(d, r, c); }
   __device__ int32_t w_int(int u, int v) const { return G::w_int(S.fa[u], S.fb[u], S.fa[v], S.fb[v], Wt_x, Wt_z); }
 };
 
-__device__ __forceinline__ void toggle(uint32_t* cfg, int w, int q, bool z_step) {
-  atomicXor(&cfg[(z_step ? w : 0) + (q >> 5)], 1u << (q & 31));
+template <class G>
+__device__ __forceinline__ void toggle(const Ctx<G>& X, uint32_t* cfg, int q, bool z_step) {
+  if (!XZZX_CHECK(X.err, q >= 0 && q < X.nq)) return;
+  atomicXor(&cfg[(z_step ? X.w : 0) + (q >> 5)], 1u << (q & 31));
 }
 
 // Canonical internal walk: a Z step toward v whenever one is still needed and
@@ -138,7 +143,7 @@ __device__ bool walk_internal(const Ctx<G>& X, int u, int v, uint32_t* cfg) {
       if (after != before - 1) continue;
       const int q = X.qubit(qr, qc);
       if (X.face(na, nb) < 0 || q < 0) continue;
-      toggle(cfg, X.w, q, z_step);
+      toggle(X, cfg, q, z_step);
       a = na;
       b = nb;
       moved = true;
@@ -167,11 +172,11 @@ __device__ bool walk_boundary(const Ctx<G>& X, int u, uint32_t* cfg) {
       const int nf = X.face(na, nb);
       if (nf < 0) {
         if (w == here) {
-          toggle(cfg, X.w, q, z_step);
+          toggle(X, cfg, q, z_step);
           return true;
         }
       } else if (X.S.wb[nf] + w == here) {
-        toggle(cfg, X.w, q, z_step);
+        toggle(X, cfg, q, z_step);
         cur = nf;
         moved = true;
         break;
@@ -200,7 +205,7 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
   for (int j = tid; j < G::at_size(d); j += blockDim.x) S.at[j] = C.face_at[j];
   for (int j = tid; j < C.sw; j += blockDim.x) S.syn[j] = syn[j];
   __syncthreads();
-  Ctx<G> X{S, d, w, Wt_x, Wt_z};
+  Ctx<G> X{S, d, w, Wt_x, Wt_z, C.err, C.nq};
 
   // Boundary distances: start from the boundary edges, relax until stable.
   for (int f = tid; f < ns; f += blockDim.x) {
@@ -246,7 +251,8 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
       const int c2 = f < ns ? C.face_c2[f] : 0;
       for (int c = 0; c < 2; ++c) {
         const uint32_t m = __ballot_sync(0xFFFFFFFFu, on && c2 == c);
-        if (on && c2 == c) S.defects[c][cnt[c] + __popc(m & ((1u << lane) - 1))] = (int16_t)f;
+        const int slot = cnt[c] + __popc(m & ((1u << lane) - 1));
+        if (on && c2 == c && XZZX_CHECK(C.err, slot < G::kMaxFaces / 2)) S.defects[c][slot] = (int16_t)f;
         cnt[c] += __popc(m);
       }
     }
@@ -283,11 +289,14 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
     __syncwarp();
     int unmatched = nv;
     while (unmatched > 0) {
-      // Each free vertex finds its best free partner in the order (w, key, u, v),
-      // in one pass: a candidate's key is drawn only when its weight ties the
-      // best so far.  A best partner that is still free stays the best (removing
-      // other vertices cannot put one ahead of it), so only vertices whose best
-      // was matched in the last round search again.
+      // Each free vertex finds its best free partner in the order (w, key, u, v).
+      // Pass 1 finds the minimum weight, the lexicographically first (u, v)
+      // reaching it and how many pairs reach it; only when several pairs tie
+      // at the minimum (and keys are random) does pass 2 draw their keys, so
+      // no key is drawn for a pair that a lighter one beats.  A best partner
+      // that is still free stays the best (removing other vertices cannot put
+      // one ahead of it), so only vertices whose best was matched in the last
+      // round search again.
       for (int x = lane; x < nv; x += 32) {
         if (partner[x] >= 0) {
           best[x] = -1;
@@ -298,41 +307,49 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
         const bool xb = x == nd;
         const int fx = xb ? 0 : D[x];
         const uint32_t sx = xb ? kBoundary : (uint32_t)fx;
-        int bestv = -1;
+        auto weight = [&](int y) -> int32_t {
+          if (xb) return S.wb[D[y]];
+          if (y == nd) return S.wb[fx];
+          return min(X.w_int(fx, D[y]), S.wb[fx] + S.wb[D[y]]);
+        };
+        int bestv = -1, ties = 0;
         int32_t bw = kInf;
-        uint32_t bkey = 0, bu = 0, bvv = 0;
-        bool bkey_ok = false;
+        uint32_t bu = 0, bvv = 0;
         for (int y = 0; y < nv; ++y) {
           if (y == x || partner[y] >= 0) continue;
-          int32_t wxy;
-          if (xb) wxy = S.wb[D[y]];
-          else if (y == nd) wxy = S.wb[fx];
-          else wxy = min(X.w_int(fx, D[y]), S.wb[fx] + S.wb[D[y]]);
+          const int32_t wxy = weight(y);
           if (wxy > bw) continue;
           const uint32_t sy = (y == nd) ? kBoundary : (uint32_t)D[y];
           const uint32_t u = min(sx, sy), v = max(sx, sy);
           if (wxy < bw) {
-            bestv = y;
             bw = wxy;
-            bu = u;
-            bvv = v;
-            bkey_ok = false;
+            ties = 0;
+          } else if (!(u < bu || (u == bu && v < bvv))) {
+            ++ties;
             continue;
           }
-          uint32_t key = 0;
-          if (mode == kInitGreedyRandom) {
-            const uint32_t c3 = kTagGreedy | ((uint32_t)(shot >> 32) << 8);
-            if (!bkey_ok) {
-              bkey = philox4x32_10(bu | (bvv << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
-              bkey_ok = true;
+          ++ties;
+          bestv = y;
+          bu = u;
+          bvv = v;
+        }
+        if (mode == kInitGreedyRandom && ties > 1) {
+          const uint32_t c3 = kTagGreedy | ((uint32_t)(shot >> 32) << 8);
+          uint32_t bkey = 0;
+          bool have = false;
+          for (int y = 0; y < nv; ++y) {
+            if (y == x || partner[y] >= 0) continue;
+            if (weight(y) != bw) continue;
+            const uint32_t sy = (y == nd) ? kBoundary : (uint32_t)D[y];
+            const uint32_t u = min(sx, sy), v = max(sx, sy);
+            const uint32_t key = philox4x32_10(u | (v << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
+            if (!have || key < bkey || (key == bkey && (u < bu || (u == bu && v < bvv)))) {
+              have = true;
+              bestv = y;
+              bkey = key;
+              bu = u;
+              bvv = v;
             }
-            key = philox4x32_10(u | (v << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
-          }
-          if (key < bkey || (key == bkey && (u < bu || (u == bu && v < bvv)))) {
-            bestv = y;
-            bkey = key;
-            bu = u;
-            bvv = v;
           }
         }
         best[x] = (int16_t)bestv;
@@ -342,7 +359,7 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
       int made = 0;
       for (int x = lane; x < nv; x += 32) {
         const int y = best[x];
-        if (y > x && best[y] == x) {
+        if (y > x && XZZX_CHECK(C.err, y < nv) && best[y] == x) {
           partner[x] = (int16_t)y;
           partner[y] = (int16_t)x;
           made += 2;
@@ -390,8 +407,13 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
     par_z ^= __shfl_xor_sync(0xFFFFFFFFu, par_z, off);
     par_x ^= __shfl_xor_sync(0xFFFFFFFFu, par_x, off);
   }
-  if (lane == 0)
-    cbits[i] = (uint8_t)(par_z | (par_x << 1) | (S.walk_error[warp] ? 0x80 : 0));
+  if (lane == 0) {
+    // A walk that could not complete is recorded in the code's error area
+    // (XZZX_DEVERR_GREEDY_WALK) and in bit 7 of the restart's class byte.
+    const bool bad = S.walk_error[warp] != 0 || (i == 0 && injected(C.err, XZZX_DEVERR_GREEDY_WALK));
+    if (bad) raise_device_error(C.err, XZZX_DEVERR_GREEDY_WALK);
+    cbits[i] = (uint8_t)(par_z | (par_x << 1) | (bad ? 0x80 : 0));
+  }
 }
 
 }  // namespace greedy

@@ -231,7 +231,8 @@ xzzx_status xzzx_make_code(int d, int layout, xzzx_code** out) {
   const size_t o_c2 = align256(o_b + sizeof(int16_t) * c->ns);
   const size_t o_at = align256(o_c2 + c->ns);
   const size_t o_log = align256(o_at + sizeof(int16_t) * c->face_at.size());
-  const size_t total = align256(o_log + sizeof(uint32_t) * c->logical.size());
+  const size_t o_err = align256(o_log + sizeof(uint32_t) * c->logical.size());
+  const size_t total = align256(o_err + sizeof(uint32_t) * kErrWords);
   if (!has_device()) {  // host tables only; launches on this handle are refused
     *out = c;
     return XZZX_OK;
@@ -268,6 +269,7 @@ xzzx_status xzzx_make_code(int d, int layout, xzzx_code** out) {
   dv.face_c2 = (const uint8_t*)(base + o_c2);
   dv.face_at = (const int16_t*)(base + o_at);
   dv.logical = (const uint32_t*)(base + o_log);
+  dv.err = (uint32_t*)(base + o_err);  // zeroed with the blob
   *out = c;
   return XZZX_OK;
 }
@@ -298,6 +300,31 @@ void xzzx_free_code(xzzx_code* code) {
   if (!code) return;
   if (code->dev_block) cudaFree(code->dev_block);
   delete code;
+}
+
+xzzx_status xzzx_device_errors(const xzzx_code* code, uint32_t* flags, uint32_t* count, int clear, void* stream) {
+  xzzx_status st = check_code(code);
+  if (st) return st;
+  const cudaStream_t s = (cudaStream_t)stream;
+  uint32_t words[2] = {0u, 0u};
+  XZZX_CUDA_TRY(cudaMemcpyAsync(words, code->dev.err, sizeof(words), cudaMemcpyDeviceToHost, s));
+  if (clear) XZZX_CUDA_TRY(cudaMemsetAsync(code->dev.err, 0, sizeof(words), s));
+  XZZX_CUDA_TRY(cudaStreamSynchronize(s));
+  if (flags) *flags = words[0];
+  if (count) *count = words[1];
+  return XZZX_OK;
+}
+
+xzzx_status xzzx_debug_inject(const xzzx_code* code, uint32_t flags, void* stream) {
+  xzzx_status st = check_code(code);
+  if (st) return st;
+  if (flags & ~(uint32_t)(XZZX_DEVERR_GREEDY_WALK | XZZX_DEVERR_BOUNDS)) return fail(XZZX_EINVAL, "unknown flag");
+  // The value lives in a stream-ordered upload from a host word that must
+  // outlive the copy: a static per flag combination.
+  static const uint32_t kValues[4] = {0u, 1u, 2u, 3u};
+  XZZX_CUDA_TRY(cudaMemcpyAsync(code->dev.err + 2, &kValues[flags], sizeof(uint32_t), cudaMemcpyHostToDevice,
+                                (cudaStream_t)stream));
+  return XZZX_OK;
 }
 
 xzzx_status xzzx_make_noise(double px, double py, double pz, int32_t scale, xzzx_noise* out) {

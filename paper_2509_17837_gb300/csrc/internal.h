@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/xzzx.h"
 
 namespace xzzx {
@@ -39,6 +41,17 @@ class DeviceOnce {
 
  private:
   std::atomic<uint64_t> done_{0};
+};
+
+// NVTX range around the host-side enqueue of one step of the path, so a
+// timeline tool shows greedy (K1), annealing (K2) and decision (K3) launches by
+// name.  Costs a few nanoseconds when no tool is attached.
+class NvtxRange {
+ public:
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 #define XZZX_CUDA_TRY(expr)                                    \
@@ -102,7 +115,33 @@ struct DevCode {
   const uint8_t* face_c2;    // ns, decoding-graph colour
   const int16_t* face_at;    // rotated (d+1)^2 at (a+1)*(d+1)+(b+1); planar (2d-1)^2 at i*(2d-1)+j; -1 = none
   const uint32_t* logical;   // 2 x 2w words: L_X then L_Z, bit planes
+  uint32_t* err;             // kErrWords: device-side error flags of work done with this code
 };
+
+// Device-side error area of a code (kErrWords words): [0] the OR of the
+// XZZX_DEVERR_* flags raised, [1] how many times one was raised, [2] flags
+// the host asks the kernels to raise as if the failure had happened (a test
+// hook that faults nothing), [3] unused.
+constexpr int kErrWords = 4;
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void raise_device_error(uint32_t* err, uint32_t flag) {
+  atomicOr(&err[0], flag);
+  atomicAdd(&err[1], 1u);
+}
+__device__ __forceinline__ bool injected(const uint32_t* err, uint32_t flag) {
+  return (*(volatile const uint32_t*)&err[2] & flag) != 0u;
+}
+#endif
+
+// Bounds checks of the XZZX_CHECKS build: a failed check raises
+// XZZX_DEVERR_BOUNDS and the caller skips the access.  The plain build
+// compiles them out.
+#ifdef XZZX_CHECKS
+#define XZZX_CHECK(err, cond) ((cond) ? true : (::xzzx::raise_device_error((err), XZZX_DEVERR_BOUNDS), false))
+#else
+#define XZZX_CHECK(err, cond) true
+#endif
 
 // Planar qubit index of site (r, c), r + c even, inside the (2d-1)^2 grid:
 // row-major over the qubit sites.

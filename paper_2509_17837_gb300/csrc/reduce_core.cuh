@@ -81,7 +81,7 @@ __device__ __forceinline__ void reduce_warp(const DevCode& C, int R, const uint3
     }
     if (lane == 0 && fail) *fail = (uint8_t)((par_z | par_x) != 0);
   }
-  if (best_cfg_out && chain_cfg) {
+  if (best_cfg_out && chain_cfg && XZZX_CHECK(C.err, (uint32_t)bstar < 4u * (uint32_t)R)) {
     const uint32_t* src = chain_cfg + (size_t)(uint32_t)bstar * 2 * w;
     for (int j = lane; j < 2 * w; j += 32) best_cfg_out[j] = src[j];
   }

@@ -99,6 +99,8 @@ struct xzzx_server {
   int64_t submitted = 0, rejected = 0, dispatched = 0, completed = 0, batches = 0;
   xzzx_status sticky = XZZX_OK;
   std::string sticky_msg;
+  uint32_t* d_err = nullptr;     // device error area shared by the classes' codes
+  uint32_t device_errors = 0;    // OR of the XZZX_DEVERR_* flags seen after batches
   std::mutex mu;
   std::condition_variable cv, cv_done;
   std::thread dispatcher;
@@ -183,6 +185,9 @@ xzzx_status issue(xzzx_server* sv, Slot& slot) {
   // has nothing to balance here.
   if ((st = launch_plan(plan, pd, sv->keys, (int)plan.lpt.size(), slot.warp_mode ? 2 : 1, slot.stream))) return st;
   XZZX_CUDA_TRY(cudaMemcpyAsync(slot.host_out, slot.dev + o_out, out_bytes, cudaMemcpyDeviceToHost, slot.stream));
+  // the device error flags after this batch, read beside its results
+  XZZX_CUDA_TRY(cudaMemcpyAsync(slot.host_out + (size_t)sv->cfg.max_batch * kOutStride, sv->d_err,
+                                2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, slot.stream));
   XZZX_CUDA_TRY(cudaLaunchHostFunc(slot.stream, on_complete, &slot));
   return XZZX_OK;
 }
@@ -208,6 +213,7 @@ void harvest(xzzx_server* sv) {
       sv->done.push_back(res);
       ++sv->completed;
     }
+    sv->device_errors |= *(const uint32_t*)(s.host_out + (size_t)sv->cfg.max_batch * kOutStride);
     sv->regs_in_use -= s.regs;
     sv->warp_inflight -= s.warps;
     s.reqs.clear();
@@ -289,6 +295,34 @@ void dispatcher_main(xzzx_server* sv) {
     if (sv->stop && sv->pending.empty() && !any_busy) break;
     if (sv->sticky) {
       if (!any_busy) break;
+      continue;
+    }
+    if (sv->stop && !any_busy && !sv->pending.empty()) {
+      // Stopping with nothing in flight: whatever cannot be dispatched now
+      // never will be (no completion is coming to free budget), so it is
+      // dropped and counted as rejected rather than waited on.
+      bool formed = false;
+      for (Slot& s : sv->slots)
+        if (!s.busy && form_batch(sv, s)) {
+          formed = true;
+          lk.unlock();
+          const xzzx_status st = issue(sv, s);
+          lk.lock();
+          if (st) {
+            sv->sticky = st;
+            sv->sticky_msg = std::string("dispatch failed: ") + xzzx_last_error();
+            sv->regs_in_use -= s.regs;
+            sv->warp_inflight -= s.warps;
+            s.reqs.clear();
+            s.regs = s.warps = 0;
+            s.busy = false;
+          }
+          break;
+        }
+      if (!formed) {
+        sv->rejected += (int64_t)sv->pending.size();
+        sv->pending.clear();
+      }
       continue;
     }
     for (Slot& s : sv->slots) {
@@ -396,6 +430,18 @@ xzzx_status xzzx_serve_start(xzzx_server* sv) {
   const size_t budget = sv->cfg.hbm_budget_bytes ? sv->cfg.hbm_budget_bytes : ((size_t)256 << 20);
   sv->slot_bytes = budget / sv->cfg.n_slots & ~(size_t)255;
   sv->staging_bytes = ((size_t)64 << 10) + (size_t)sv->cfg.max_batch * 1024;
+  // Every class must fit one request into an empty slot (memory and staging),
+  // or requests of that class could never be dispatched.
+  for (const Class& c : sv->classes)
+    if (4096 + c.bytes > sv->slot_bytes || 4096 + c.bytes > sv->staging_bytes)
+      return fail(XZZX_ENOMEM, "one request of distance " + std::to_string(c.d) + " needs " +
+                                   std::to_string(4096 + c.bytes) + " bytes but a slot holds " +
+                                   std::to_string(sv->slot_bytes) + " (raise hbm_budget_bytes or lower n_slots)");
+  // One device error area for every class's code, so that each batch's flags
+  // can be read back with its results.
+  XZZX_CUDA_TRY(cudaMalloc((void**)&sv->d_err, 256));
+  XZZX_CUDA_TRY(cudaMemset(sv->d_err, 0, 256));
+  for (Class& c : sv->classes) c.code->dev.err = sv->d_err;
   sv->slots.resize(sv->cfg.n_slots);
   for (int i = 0; i < sv->cfg.n_slots; ++i) {
     Slot& s = sv->slots[i];
@@ -404,7 +450,7 @@ xzzx_status xzzx_serve_start(xzzx_server* sv) {
     cudaError_t e = cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc((void**)&s.dev, sv->slot_bytes);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&s.host_in, sv->staging_bytes);
-    if (e == cudaSuccess) e = cudaMallocHost((void**)&s.host_out, (size_t)sv->cfg.max_batch * kOutStride);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&s.host_out, (size_t)sv->cfg.max_batch * kOutStride + 256);
     if (e != cudaSuccess) return cuda_fail(e, "xzzx_serve_start slot allocation");
   }
   sv->started = true;
@@ -499,6 +545,7 @@ xzzx_status xzzx_serve_get_stats(xzzx_server* sv, xzzx_serve_stats* out, int res
   out->pending = (int64_t)sv->pending.size();
   for (const Slot& s : sv->slots) out->in_flight += (int64_t)s.reqs.size();
   out->mean_batch = sv->batches ? (double)sv->dispatched / sv->batches : 0.0;
+  out->device_errors = sv->device_errors;
   if (!sv->lat_us.empty()) {
     std::vector<double> v = sv->lat_us;
     std::sort(v.begin(), v.end());
@@ -536,6 +583,7 @@ void xzzx_serve_destroy(xzzx_server* sv) {
     if (s.host_in) cudaFreeHost(s.host_in);
     if (s.host_out) cudaFreeHost(s.host_out);
   }
+  if (sv->d_err) cudaFree(sv->d_err);
   for (Class& c : sv->classes) {
     xzzx_free_schedule(c.sched);
     xzzx_free_code(c.code);

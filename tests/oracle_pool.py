@@ -64,3 +64,18 @@ def decode_shots(task):
         for k in keys:
             acc[k].append(out[k][0])
     return {k: np.array(v) for k, v in acc.items()}
+
+
+def anneal_one_chain(task):
+    """The oracle's greedy reference R_i of one (shot, restart), its class
+    bits, and the best energy of chain (shot, restart, coset P) annealed from
+    R_i L_P.  task = (code_id, (px, py, pz), scale, n_sweeps, beta0, beta1,
+    seed, restarts, shot, restart, P); linear schedule, Alg. 6 references."""
+    import oracle as O
+    d, pxyz, scale, N, b0, b1, seed, R, s, i, P = task
+    _, syn = O.sample(d, pxyz, seed, s, 1)
+    Ri, _ = O.greedy(d, pxyz, scale, seed, s, i, 1, syn[0])
+    LX, LZ = O.logicals(d)
+    L = [0 * LX, LX, LX ^ LZ, LZ][P]
+    ref = O.anneal_chain(d, pxyz, scale, O.LINEAR, N, b0, b1, seed, (s * R + i) * 4 + P, Ri ^ L)
+    return Ri, O.class_bits(d, Ri), ref["best_E"]

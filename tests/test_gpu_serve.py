@@ -143,3 +143,19 @@ def test_full_queue_rejects(env):
         assert st["rejected"] == codes.count(XZZX_EBUSY) and st["completed"] == accepted == len(res)
     finally:
         sv.close()
+
+
+def test_slot_too_small_for_one_request_is_refused(env):
+    """A budget whose slots cannot hold one request of a registered class is
+    refused at start (XZZX_ENOMEM) instead of leaving that class's requests
+    waiting forever; closing the refused server returns."""
+    X, torch = env
+    from paper_2509_17837_gb300._lib import XZZX_ENOMEM
+    sv = X.Server(SEED, 64, N, B0, B1, max_batch=16, n_slots=8, hbm_budget_bytes=64 << 10)
+    try:
+        sv.add_class(21, X.noise_from_eta(0.1, 10))
+        with pytest.raises(X.XzzxError) as e:
+            sv.start()
+        assert e.value.status == XZZX_ENOMEM
+    finally:
+        sv.close()
