@@ -827,7 +827,7 @@ def main():
         }
     # ---------------------------------------------------------------- greedy-only decisions (0 sweeps)
     # The same shots decided from the 256 initial configurations R_i L_P alone
-    # (no annealing): the logical error rate SA improves on.
+    # (no annealing), as the baseline the annealing is compared with.
     if not args.no_greedy_only:
         fails0 = [0] * len(PS)
         for ci, c in enumerate(cases):
@@ -845,6 +845,24 @@ def main():
         if rank == 0:
             result["logical_error_rates_greedy_only"] = [stats.ler_record(p, f, S * args.steps * world)
                                                          for p, f in zip(PS, fails0)]
+        # Context for the schedule: the last step's shots decoded again with the
+        # annealing starting at 0.9 beta_N (the start of the paper's own
+        # schedule) instead of 0.05, same 1000 sweeps and end point.
+        fails9 = [0] * len(PS)
+        k = n_steps - 1
+        for ci, c in enumerate(cases):
+            sched9 = X.Schedule(c["noise"], SWEEPS, 0.9, BETA1)
+            s0 = k * S
+            X.greedy_init(code, c["noise"], c["seed"], c["shot_base"] + s0, c["syn"][s0:s0 + S], RESTARTS,
+                          init=init, cbits=cbits, stream=stream)
+            X.anneal(code, sched9, c["seed"], c["shot_base"] + s0, init, want_cfg=False, best_E=chain_E,
+                     stream=stream)
+            r9 = X.decode_reduce(code, init, cbits, chain_E, true_errors=c["err"][s0:s0 + S], stream=stream)
+            fails9[ci] += int(r9["fail"].sum())
+        if world > 1:
+            fails9 = [int(f) for f in sum_over_ranks([float(f) for f in fails9], dist, dev)]
+        if rank == 0:
+            result["logical_error_rates_beta0_0.9"] = [stats.ler_record(p, f, S * world) for p, f in zip(PS, fails9)]
     # ---------------------------------------------------------------- oracle parity (rank 0)
     if rank == 0 and parity.pool is not None:
         result["parity"] = parity.compare(last_outs, code.words)

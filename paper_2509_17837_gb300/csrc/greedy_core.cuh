@@ -289,14 +289,11 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
     __syncwarp();
     int unmatched = nv;
     while (unmatched > 0) {
-      // Each free vertex finds its best free partner in the order (w, key, u, v).
-      // Pass 1 finds the minimum weight, the lexicographically first (u, v)
-      // reaching it and how many pairs reach it; only when several pairs tie
-      // at the minimum (and keys are random) does pass 2 draw their keys, so
-      // no key is drawn for a pair that a lighter one beats.  A best partner
-      // that is still free stays the best (removing other vertices cannot put
-      // one ahead of it), so only vertices whose best was matched in the last
-      // round search again.
+      // Each free vertex finds its best free partner in the order (w, key, u, v),
+      // in one pass: a candidate's key is drawn only when its weight ties the
+      // best so far.  A best partner that is still free stays the best (removing
+      // other vertices cannot put one ahead of it), so only vertices whose best
+      // was matched in the last round search again.
       for (int x = lane; x < nv; x += 32) {
         if (partner[x] >= 0) {
           best[x] = -1;
@@ -307,49 +304,41 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
         const bool xb = x == nd;
         const int fx = xb ? 0 : D[x];
         const uint32_t sx = xb ? kBoundary : (uint32_t)fx;
-        auto weight = [&](int y) -> int32_t {
-          if (xb) return S.wb[D[y]];
-          if (y == nd) return S.wb[fx];
-          return min(X.w_int(fx, D[y]), S.wb[fx] + S.wb[D[y]]);
-        };
-        int bestv = -1, ties = 0;
+        int bestv = -1;
         int32_t bw = kInf;
-        uint32_t bu = 0, bvv = 0;
+        uint32_t bkey = 0, bu = 0, bvv = 0;
+        bool bkey_ok = false;
         for (int y = 0; y < nv; ++y) {
           if (y == x || partner[y] >= 0) continue;
-          const int32_t wxy = weight(y);
+          int32_t wxy;
+          if (xb) wxy = S.wb[D[y]];
+          else if (y == nd) wxy = S.wb[fx];
+          else wxy = min(X.w_int(fx, D[y]), S.wb[fx] + S.wb[D[y]]);
           if (wxy > bw) continue;
           const uint32_t sy = (y == nd) ? kBoundary : (uint32_t)D[y];
           const uint32_t u = min(sx, sy), v = max(sx, sy);
           if (wxy < bw) {
+            bestv = y;
             bw = wxy;
-            ties = 0;
-          } else if (!(u < bu || (u == bu && v < bvv))) {
-            ++ties;
+            bu = u;
+            bvv = v;
+            bkey_ok = false;
             continue;
           }
-          ++ties;
-          bestv = y;
-          bu = u;
-          bvv = v;
-        }
-        if (mode == kInitGreedyRandom && ties > 1) {
-          const uint32_t c3 = kTagGreedy | ((uint32_t)(shot >> 32) << 8);
-          uint32_t bkey = 0;
-          bool have = false;
-          for (int y = 0; y < nv; ++y) {
-            if (y == x || partner[y] >= 0) continue;
-            if (weight(y) != bw) continue;
-            const uint32_t sy = (y == nd) ? kBoundary : (uint32_t)D[y];
-            const uint32_t u = min(sx, sy), v = max(sx, sy);
-            const uint32_t key = philox4x32_10(u | (v << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
-            if (!have || key < bkey || (key == bkey && (u < bu || (u == bu && v < bvv)))) {
-              have = true;
-              bestv = y;
-              bkey = key;
-              bu = u;
-              bvv = v;
+          uint32_t key = 0;
+          if (mode == kInitGreedyRandom) {
+            const uint32_t c3 = kTagGreedy | ((uint32_t)(shot >> 32) << 8);
+            if (!bkey_ok) {
+              bkey = philox4x32_10(bu | (bvv << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
+              bkey_ok = true;
             }
+            key = philox4x32_10(u | (v << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
+          }
+          if (key < bkey || (key == bkey && (u < bu || (u == bu && v < bvv)))) {
+            bestv = y;
+            bkey = key;
+            bu = u;
+            bvv = v;
           }
         }
         best[x] = (int16_t)bestv;

@@ -34,18 +34,25 @@ def chunks(lo, hi, n):
 def bruteforce_vs_sa(task):
     """Decode shots [s0, s1) with the oracle and compare each shot's coset
     energies with the exact coset minima found by enumerating the stabilizer
-    group.  Returns per-shot (E4 from SA, exact E4, cls from SA)."""
+    group.  Returns per-shot (E4 from SA, exact E4, cls from SA, SA failure
+    flag, failure flag of the exact minimum-energy decision, failure flag of
+    the decision from the initial configurations alone (0 sweeps))."""
     import oracle as O
     c, s0, s1 = task
     pxyz = O.noise_from_eta(c["p"], c["eta"])
     err, syn = O.sample(c["d"], pxyz, c["seed"], s0, s1 - s0)
     out = O.decode(c["d"], pxyz, c["scale"], O.LINEAR, c["sweeps"], c["b0"], c["b1"], c["seed"], s0,
                    c["restarts"], syn, err)
+    none = O.decode(c["d"], pxyz, c["scale"], O.LINEAR, 0, c["b0"], c["b1"], c["seed"], s0, c["restarts"], syn, err)
+    LX, LZ = O.logicals(c["d"])
+    Ls = [0 * LX, LX, LX ^ LZ, LZ]
     exact = np.zeros((s1 - s0, 4), np.int32)
+    med_fail = np.zeros(s1 - s0, np.uint8)
     for i in range(s1 - s0):
         R1, _ = O.greedy(c["d"], pxyz, c["scale"], c["seed"], s0 + i, 0, 1, syn[i])
         exact[i] = O.bruteforce(c["d"], pxyz, c["scale"], R1)
-    return out["E4"], exact, out["cls"]
+        med_fail[i] = O.class_bits(c["d"], err[i] ^ R1 ^ Ls[int(np.argmin(exact[i]))]) != 0
+    return out["E4"], exact, out["cls"], out["fail"], med_fail, none["fail"]
 
 
 def decode_shots(task):
