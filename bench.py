@@ -32,21 +32,19 @@ sys.path.insert(0, ROOT)
 D, ETA, PS, RESTARTS, SWEEPS, BETA0, BETA1, SCALE = 11, 100.0, (0.10, 0.13, 0.16, 0.19, 0.22), 64, 1000, 0.05, 20.0, 1024
 SEED = 0xD11
 I_ALG = 30  # integer instructions per move attempt in the algorithmic count
-# DRAM bytes (read + write) per chain of anneal_kernel<11>, from one ncu
-# capture of the current kernel (128,000 chains, 1.4738e6 B): each chain reads
-# its 32-byte reference (shared by its four cosets) and writes 4 bytes, which
-# stay in L2.
-ANNEAL_DRAM_BYTES_PER_CHAIN = 1.4738e6 / 128000
-# ALU-pipe lane instructions per attempt of anneal_kernel<11> (ncu
-# sm__inst_executed_pipe_alu of the same capture x 32 / attempts); the ALU
-# pipe takes 16 lanes per clock per SM sub-partition.
-ANNEAL_ALU_INST_PER_ATTEMPT = 15.3
-# Counters of the same capture, per move attempt: lane instructions issued
-# (smsp__inst_executed x 32), and shared-memory bank conflicts per shared
-# wavefront.
-ANNEAL_MEASURED = {"inst_per_attempt": 25.5, "alu_inst_per_attempt": ANNEAL_ALU_INST_PER_ATTEMPT,
-                   "shared_bank_conflicts_per_wavefront": 1.45e9 / 2.59e9,
-                   "source": "ncu capture of one anneal_kernel<11> launch, profiles/anneal_d11_ncu_full.md"}
+# Counters of the current anneal_kernel<11> from one ncu capture (None until
+# the kernel has been captured since its last change): DRAM bytes (read +
+# write) per chain, ALU-pipe lane instructions per move attempt
+# (sm__inst_executed_pipe_alu x 32 / attempts; the ALU pipe takes 16 lanes per
+# clock per SM sub-partition), all lane instructions per attempt
+# (smsp__inst_executed x 32 / attempts) and shared-memory bank conflicts per
+# shared wavefront.
+ANNEAL_DRAM_BYTES_PER_CHAIN = 8.368384e6 / 1.024e6
+ANNEAL_ALU_INST_PER_ATTEMPT = 12.12
+ANNEAL_MEASURED = {"inst_per_attempt": 20.96, "alu_inst_per_attempt": ANNEAL_ALU_INST_PER_ATTEMPT,
+                   "shared_bank_conflicts_per_wavefront": 1.2124e10 / 2.1612e10,
+                   "source": "ncu capture of one anneal_kernel<11> launch of 4000 shots, "
+                             "profiles/anneal_d11_ncu_full.md"}
 
 
 def workload_config(shots_per_p, world):
@@ -352,17 +350,16 @@ def run_uneven(args):
     from paper_2509_17837_gb300 import autotune
     seed = 0xF1
     segs = uneven_segments(X, args.uneven_shots, seed)
-    tune_segs = uneven_segments(X, args.uneven_shots, seed, scale_shots=0.125)
-    cfg, timings = autotune.tune(lambda c, o: X.Batch(tune_segs, seed, ctas_per_sm=c, order=o), tune_segs,
-                                 candidates=[(0, 0, 0), (0, 0, 1), (0, 1, 0), (0, 2, 0), (0, 3, 0), (1, 0, 0),
-                                             (2, 0, 0), (3, 0, 0)], use_cache=False)
-    # the persistent launch (the form this workload measures) with the tuned grid and order
-    best_persistent = min((k for k in timings if k.startswith("0,")), key=timings.get)
-    _, cps, order = (int(x) for x in best_persistent.split(","))
-    batch = X.Batch(segs, seed, ctas_per_sm=cps, order=order)
-    info = batch.info()
-    stream = torch.cuda.Stream()
+    # the tuner times short runs of a same-shaped batch of at most ~20k shots
+    tune_scale = min(1.0, 20000.0 / args.uneven_shots)
+    tune_segs = uneven_segments(X, args.uneven_shots, seed, scale_shots=tune_scale)
+    cfg, timings = autotune.tune(
+        lambda c, o, nt, u: X.Batch(tune_segs, seed, ctas_per_sm=c, order=o, chains_per_cta=nt, sweep_unroll=u),
+        tune_segs, use_cache=False)
+    knobs = lambda key: tuple(int(x) for x in key.split(","))
+    best_of = lambda modes: knobs(min((k for k in timings if knobs(k)[0] in modes), key=timings.get))
     dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
 
     def timed(fn, steps, warmup):
@@ -381,47 +378,60 @@ def run_uneven(args):
             ms += e0.elapsed_time(e1)
         return ms / steps
 
-    conc = X.Batch(segs, seed, graph_mode=3)
+    def form(mode, cps, order, nt, u):
+        """A batch in one of the forms, and the call that runs it (modes 0 and 3
+        as captured graphs)."""
+        b = X.Batch(segs, seed, ctas_per_sm=cps, order=order, graph_mode=3 if mode == 3 else 0,
+                    chains_per_cta=nt, sweep_unroll=u)
+        run = (lambda: b.run_graph(stream)) if mode in (0, 3) else (lambda: b.run(mode, stream))
+        return b, run
+
     sampler = ClockSampler(args.clocks_csv, dev)
     sampler.start()
-    with torch.cuda.stream(stream):
-        ms_batched = timed(lambda: batch.run_graph(stream), args.steps, args.warmup)
-        out_b = [{k: (v.clone() if v is not None else None) for k, v in o.items()} for o in batch.outputs]
-        ms_plain = timed(lambda: batch.run(1, stream), args.steps, 1)
-        ms_conc = timed(lambda: conc.run_graph(stream), args.steps, 1)
-    stream.synchronize()
+    forms = {"tuned": cfg, "persistent": best_of((0,)), "concurrent": best_of((3,)), "plain": (1, 0, 0, 128, 1)}
+    ms, outs, info = {}, {}, None
+    for name, (mode, cps, order, nt, u) in forms.items():
+        b, run = form(mode, cps, order, nt, u)
+        with torch.cuda.stream(stream):
+            ms[name] = timed(run, args.steps, args.warmup)
+        stream.synchronize()
+        outs[name] = [{k: (v.clone() if v is not None else None) for k, v in o.items()} for o in b.outputs]
+        if name == "tuned":
+            info = b.info()
+        b.close()
     clocks = sampler.stop()
-    same = all(torch.equal(a[k], b[k]) for a, b in zip(out_b, batch.outputs) for k in a if a[k] is not None)
-    same = same and all(torch.equal(a[k], b[k]) for a, b in zip(out_b, conc.outputs) for k in a if a[k] is not None)
-    fails = sum(int(o["fail"].sum()) for o in batch.outputs)
+    ref = outs["plain"]
+    same = all(torch.equal(a[k], r[k]) for name in outs for a, r in zip(outs[name], ref) for k in r
+               if r[k] is not None)
+    fails = sum(int(o["fail"].sum()) for o in ref)
     shots = info["total_shots"]
     props = torch.cuda.get_device_properties(dev)
-    att = info["move_attempts"] / (ms_batched / 1e3)
+    att = info["move_attempts"] / (ms["tuned"] / 1e3)
+    form_rec = lambda name: {"cfg": dict(zip(("mode", "ctas_per_sm", "order", "chains_per_cta", "sweep_unroll"),
+                                             forms[name])),
+                             "ms_per_step": ms[name], "shots_per_s": shots / (ms[name] / 1e3),
+                             "speedup_vs_plain": ms["plain"] / ms[name]}
     print(json.dumps({
-        "metric": "decoded shots/s, uneven batch (d in {5,7,9,13,17,21}, persistent launch vs one launch per distance)",
-        "value": shots / (ms_batched / 1e3), "unit": "shots/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_batched, "higher_is_better": True, "scaling": "weak",
+        "metric": "decoded shots/s, uneven batch (d in {5,7,9,13,17,21}; tuned batched form vs one launch per distance)",
+        "value": shots / (ms["tuned"] / 1e3), "unit": "shots/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms["tuned"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int32", "data": "synthetic (seeded per-shot eta and p; library sampler)",
         "config": {"workload": "uneven batch: %d shots, distances {5,7,9,13,17,21} equal, eta in {1,10,100}, "
                                "p in [0.08,0.20] (0.005 grid), restarts {16,16,32,32,64,64}, sweeps "
                                "{500,500,1000,1000,2000,2000}, linear beta 0.05->20" % shots,
                    "segments": info["n_segments"], "chunks": info["n_chunks"],
-                   "persistent_grid": info["persistent_grid"],
-                   "autotuned_cfg": {"mode": cfg[0], "ctas_per_sm": cfg[1], "order": cfg[2],
-                                     "modes": "0 persistent thread/chain, 1 per-distance thread/chain, "
-                                              "2 per-distance warp/chain, 3 per-distance launches on forked "
-                                              "streams"},
-                   "persistent_cfg": {"ctas_per_sm": cps, "order": order},
-                   "autotune_s": timings, "l2": "flushed between steps"},
-        "move_attempts_per_s": att, "plain_ms_per_step": ms_plain, "plain_shots_per_s": shots / (ms_plain / 1e3),
-        "speedup_vs_plain": ms_plain / ms_batched, "identical_outputs": bool(same),
-        "concurrent_graph": {"ms_per_step": ms_conc, "shots_per_s": shots / (ms_conc / 1e3),
-                             "speedup_vs_plain": ms_plain / ms_conc,
-                             "form": "each distance's own kernel on forked streams, captured as one graph"},
-        "launches": {"batched_graph": info["launches_batched"], "plain": info["launches_plain"]},
+                   "tuned_cfg": form_rec("tuned")["cfg"],
+                   "modes": "0 persistent (one chain per thread, chunk queue), 1 one launch per distance, 2 per "
+                            "distance with one warp per chain, 3 per-distance launches on forked streams; 0 and 3 "
+                            "replayed as captured CUDA graphs",
+                   "autotune": {"batch_shots": int(sum(int(sg["syndromes"].shape[0]) for sg in tune_segs)),
+                                "timings_s": timings},
+                   "l2": "flushed between steps"},
+        "move_attempts_per_s": att, "forms": {name: form_rec(name) for name in forms},
+        "speedup_vs_plain": ms["plain"] / ms["tuned"], "identical_outputs": bool(same),
         "logical_failures": fails, "clocks": clocks,
         "roofline": roofline_record(att, clocks, props.multi_processor_count, traffic=None,
-                                    kernel="persistent annealing launch (all distances)")}))
+                                    kernel="annealing launches of the tuned form (all distances)")}))
 
 
 # --------------------------------------------------------------------------- serving (NEXT f2)
@@ -556,6 +566,32 @@ def run_large(args):
         mapping[name] = {"anneal_ms": e0.elapsed_time(e1),
                          "attempts_per_s": S * 4 * R * N * (d * d - 1) / (e0.elapsed_time(e1) / 1e3)}
     mapping["identical_chain_minima"] = bool(torch.equal(best["thread_per_chain"], best["warp_per_chain"]))
+
+    # Occupancy sweep, one chain per thread: the same shots as one persistent
+    # launch with a given number of chains in flight per SM (CTAs per SM x
+    # chains per CTA).  Decisions must equal the plain decode of the same shots.
+    ref = X.decode_batch(code, noise, sched, sd, S, syn[S:2 * S], R, true_errors=err[S:2 * S], stream=stream)
+    occupancy = []
+    if not args.no_occupancy_sweep:
+        for nt, cps in ((128, 1), (128, 2), (128, 3), (256, 1)):
+            seg = dict(code=code, noise=noise, sched=sched, shot0=S, syndromes=syn[S:2 * S], restarts=R,
+                       true_errors=err[S:2 * S])
+            b = X.Batch([seg], sd, ctas_per_sm=cps, chains_per_cta=nt)
+            b.run(0, stream)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(0, stream)
+            e1.record(stream)
+            e1.synchronize()
+            o = b.outputs[0]
+            same = all(torch.equal(o[k], ref[k]) for k in ("cls", "E4", "recovery", "fail"))
+            info = b.info()
+            in_flight = info["persistent_grid"] * nt // props.multi_processor_count
+            occupancy.append({"chains_per_cta": nt, "ctas_per_sm": cps, "chains_in_flight_per_sm": in_flight,
+                              "ms": e0.elapsed_time(e1),
+                              "attempts_per_s": info["move_attempts"] / (e0.elapsed_time(e1) / 1e3),
+                              "identical_decisions": bool(same)})
+            b.close()
     print(json.dumps({
         "metric": "move-attempts/s and decoded shots/s at d=31 (256 restarts, 1e4 sweeps)",
         "value": att, "unit": "move-attempts/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
@@ -565,7 +601,7 @@ def run_large(args):
                                "1e4 sweeps, linear beta 0.02->30, scale 4096", "shots_per_p_per_step": S},
         "shots_per_s": shots / (ms / 1e3), "shots_timed": shots * args.steps,
         "logical_error_rates": [stats.ler_record(p, f, S * args.steps) for p, f in zip(LARGE_PS, fails)],
-        "chain_mapping": mapping, "clocks": clocks,
+        "chain_mapping": mapping, "occupancy_sweep": occupancy, "clocks": clocks,
         "roofline": roofline_record(att, clocks, props.multi_processor_count, traffic=None,
                                     kernel="anneal_kernel<31>")}))
 
@@ -665,7 +701,8 @@ def main():
     ap.add_argument("--ler-shots", type=int, default=100000)
     ap.add_argument("--layout", default="rotated", choices=["rotated", "planar"])
     ap.add_argument("--large-shots-per-p", type=int, default=57)
-    ap.add_argument("--uneven-shots", type=int, default=60000)
+    ap.add_argument("--no-occupancy-sweep", action="store_true")
+    ap.add_argument("--uneven-shots", type=int, default=1000000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)
     ap.add_argument("--serve-max-requests", type=int, default=30000)
     ap.add_argument("--serve-max-batch", type=int, default=1024)
@@ -803,10 +840,11 @@ def main():
         n_sm = props.multi_processor_count
         f_mhz = (clocks or {}).get("sm_mhz")
         roof = roofline_record(
-            anneal_rate, clocks, n_sm, traffic=ANNEAL_DRAM_BYTES_PER_CHAIN * S * RESTARTS * 4,
+            anneal_rate, clocks, n_sm,
+            traffic=None if ANNEAL_DRAM_BYTES_PER_CHAIN is None else ANNEAL_DRAM_BYTES_PER_CHAIN * S * RESTARTS * 4,
             kernel="anneal_kernel<11>",
             measured_per_attempt=ANNEAL_MEASURED,
-            secondary_alu_pipe=None if not f_mhz else {
+            secondary_alu_pipe=None if not (f_mhz and ANNEAL_ALU_INST_PER_ATTEMPT) else {
                 "alu_inst_per_attempt": ANNEAL_ALU_INST_PER_ATTEMPT,
                 "peak_attempts_per_s": n_sm * 4 * 16 * f_mhz * 1e6 / ANNEAL_ALU_INST_PER_ATTEMPT,
                 "frac": anneal_rate / (n_sm * 4 * 16 * f_mhz * 1e6 / ANNEAL_ALU_INST_PER_ATTEMPT)})

@@ -298,9 +298,11 @@ typedef struct {
 } xzzx_segment;
 
 typedef struct {
-  int32_t ctas_per_sm; /* persistent grid = SMs x this; 0 = the occupancy maximum */
-  int32_t order;       /* chunk queue: 0 = longest chunks first, 1 = segment order */
-  int32_t graph_mode;  /* the mode xzzx_batch_run_graph captures: 0 or 3 */
+  int32_t ctas_per_sm;    /* persistent grid = SMs x this; 0 = the occupancy maximum */
+  int32_t order;          /* chunk queue: 0 = longest chunks first, 1 = segment order */
+  int32_t graph_mode;     /* the mode xzzx_batch_run_graph captures: 0 or 3 */
+  int32_t chains_per_cta; /* chains per CTA of the annealing launches (chunk size): 128 or 256; 0 = 128 */
+  int32_t sweep_unroll;   /* unroll of the annealing kernels' sweep loop: 1 or 2; 0 = 1 */
 } xzzx_batch_cfg;
 
 typedef struct {
@@ -309,12 +311,15 @@ typedef struct {
   size_t workspace_bytes;
   double move_attempts;  /* per run */
   int64_t total_shots;
+  int32_t chains_per_cta, sweep_unroll;
 } xzzx_batch_info;
 
 typedef struct xzzx_batch xzzx_batch;
 
 /* Plan a batch (Alg. 7 applied to every segment).  Chains are cut into chunks
- * of 128 chains of one segment.  The batch owns its descriptors and the
+ * of cfg->chains_per_cta (128 or 256) chains of one segment, one CTA each;
+ * the chunk size and the sweep unroll are tuning knobs that never change a
+ * result (XZZX_EINVAL for other values).  The batch owns its descriptors and the
  * intermediates of every segment (one device allocation).  seed keys every
  * draw; cfg may be NULL. */
 xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t seed, const xzzx_batch_cfg* cfg,

@@ -40,13 +40,15 @@ class Segment(C.Structure):
 
 
 class BatchCfg(C.Structure):
-    _fields_ = [("ctas_per_sm", C.c_int32), ("order", C.c_int32), ("graph_mode", C.c_int32)]
+    _fields_ = [("ctas_per_sm", C.c_int32), ("order", C.c_int32), ("graph_mode", C.c_int32),
+                ("chains_per_cta", C.c_int32), ("sweep_unroll", C.c_int32)]
 
 
 class BatchInfo(C.Structure):
     _fields_ = [("n_segments", C.c_int32), ("n_chunks", C.c_int32), ("n_distances", C.c_int32),
                 ("persistent_grid", C.c_int32), ("launches_batched", C.c_int32), ("launches_plain", C.c_int32),
-                ("workspace_bytes", C.c_size_t), ("move_attempts", C.c_double), ("total_shots", C.c_int64)]
+                ("workspace_bytes", C.c_size_t), ("move_attempts", C.c_double), ("total_shots", C.c_int64),
+                ("chains_per_cta", C.c_int32), ("sweep_unroll", C.c_int32)]
 
 
 class ServeCfg(C.Structure):

@@ -244,7 +244,7 @@ class Batch:
     replays graph_mode (0 or 3) as a captured CUDA graph.
     """
 
-    def __init__(self, segments, seed, ctas_per_sm=0, order=0, graph_mode=0):
+    def __init__(self, segments, seed, ctas_per_sm=0, order=0, graph_mode=0, chains_per_cta=0, sweep_unroll=0):
         self.segments = segments
         self.outputs = []
         arr = (Segment * len(segments))()
@@ -267,7 +267,7 @@ class Batch:
             a.E4 = out["E4"].data_ptr() if n else None
             a.recovery = out["recovery"].data_ptr() if n else None
             a.fail = out["fail"].data_ptr() if out["fail"] is not None and n else None
-        cfg = BatchCfg(ctas_per_sm, order, graph_mode)
+        cfg = BatchCfg(ctas_per_sm, order, graph_mode, chains_per_cta, sweep_unroll)
         h = C.c_void_p()
         call("xzzx_batch_create", arr, len(segments), seed, C.byref(cfg), C.byref(h))
         self._h = h

@@ -9,22 +9,26 @@ It picks, for a batch shape, by timing short runs:
   launch, concurrently on forked streams;
 * for mode 0, the persistent grid in CTAs per SM (how many chains are in
   flight per SM; 0 = the occupancy limit) and the order of the chunk queue
-  (0 = longest chunks first, 1 = segment order).
+  (0 = longest chunks first, 1 = segment order);
+* the chains per CTA of the annealing launches (128 or 256: the chunk size,
+  one CTA per chunk) and the unroll of the kernels' sweep loop (1 or 2), each
+  a separately compiled kernel variant.
 
 The choice is cached in a JSON file keyed by GPU name and batch shape.  The
-knobs only change scheduling: every choice decodes bit-identically.  (The
-chains per CTA of each kernel and the unroll of its sweep loop are fixed at
-compile time at the values measured fastest.)
+knobs only change scheduling and code shape: every choice decodes
+bit-identically.
 """
 import json
 import os
 import time
 
 CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
-KEY_VERSION = "v2"
+KEY_VERSION = "v3"
 
-# (mode, ctas_per_sm, order)
-DEFAULT_CANDIDATES = [(0, c, o) for c in (0, 1, 2, 3, 4) for o in (0, 1)] + [(1, 0, 0), (2, 0, 0), (3, 0, 0)]
+# (mode, ctas_per_sm, order, chains_per_cta, sweep_unroll)
+DEFAULT_CANDIDATES = ([(0, c, o, nt, 1) for c in (0, 2, 4) for o in (0, 1) for nt in (128, 256)] +
+                      [(0, 0, 0, nt, 2) for nt in (128, 256)] +
+                      [(m, 0, 0, nt, u) for m in (1, 3) for nt in (128, 256) for u in (1, 2)] + [(2, 0, 0, 128, 1)])
 
 
 def _load(path):
@@ -57,11 +61,13 @@ _CURRENT = object()
 
 def tune(make_batch, segments, candidates=None, reps=1, use_cache=True, cache_path=None, device_name=None,
          stream=_CURRENT, sync=None):
-    """Time each candidate (mode, ctas_per_sm, order) and return (best, timings).
+    """Time each candidate (mode, ctas_per_sm, order, chains_per_cta,
+    sweep_unroll) and return (best, timings).
 
-    make_batch(ctas_per_sm, order) -> an object with run(mode, stream) and
-    close().  stream / sync default to the current CUDA stream and
-    torch.cuda.synchronize; device_name to the current GPU's name.
+    make_batch(ctas_per_sm, order, chains_per_cta, sweep_unroll) -> an object
+    with run(mode, stream) and close().  stream / sync default to the current
+    CUDA stream and torch.cuda.synchronize; device_name to the current GPU's
+    name.
     """
     if device_name is None or stream is _CURRENT or sync is None:
         import torch
@@ -74,8 +80,9 @@ def tune(make_batch, segments, candidates=None, reps=1, use_cache=True, cache_pa
     if use_cache and key in cache:
         return tuple(cache[key]["cfg"]), cache[key].get("timings", {})
     timings = {}
-    for mode, cps, order in (candidates or DEFAULT_CANDIDATES):
-        b = make_batch(cps, order)
+    for cand in (candidates or DEFAULT_CANDIDATES):
+        mode, cps, order, nt, unroll = cand
+        b = make_batch(cps, order, nt, unroll)
         try:
             b.run(mode, stream)  # warm-up
             sync()
@@ -83,7 +90,7 @@ def tune(make_batch, segments, candidates=None, reps=1, use_cache=True, cache_pa
             for _ in range(reps):
                 b.run(mode, stream)
             sync()
-            timings["%d,%d,%d" % (mode, cps, order)] = (time.perf_counter() - t0) / reps
+            timings[",".join(str(x) for x in cand)] = (time.perf_counter() - t0) / reps
         finally:
             b.close()
     best = min(timings, key=timings.get)

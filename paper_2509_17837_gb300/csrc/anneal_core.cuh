@@ -4,28 +4,43 @@
 // multi-distance kernel all call anneal_cta<D, NT>, so every launch form runs
 // the same instruction stream on the same state and gives identical results.
 //
-// State.  A chain lives in registers as one word per lattice row, two bits per
-// qubit (bit 2c = Z bit, bit 2c+1 = X bit of column c): 32-bit rows for d <= 15,
-// 64-bit rows up to d = 31.  The four corners of face (a, b) are then the
-// 4-bit fields at bit 2b of rows a and a+1, and applying G_f is two XORs with
-// fixed masks.
+// State, d > 15 ("rows").  A chain lives in registers as one 64-bit word per
+// lattice row, two bits per qubit (bit 2c = Z bit, bit 2c+1 = X bit of column
+// c).  The four corners of face (a, b) are then the 4-bit fields at bit 2b of
+// rows a and a+1, and applying G_f is two XORs with fixed masks.
+//
+// State, d <= 15 ("pairs").  Two lattice rows share one pair word, four bits
+// per column: bits [4c, 4c+2) hold (z, x) of column c of the first row, bits
+// [4c+2, 4c+4) those of the second row; a pair word takes two 32-bit registers
+// for d >= 9.  The even layout pairs rows (2j, 2j+1), the odd layout rows
+// (2j-1, 2j) (row -1 and row d are empty).  Faces of colours 0 and 2 sit on
+// even rows a, faces of colours 1 and 3 on odd ones, so in the layout of its
+// colour the 8-bit signature of face (a, b) is one byte of one pair word, at
+// bit 4b, and a move is one XOR.  The layout changes at each colour boundary
+// (two shifts and a masked merge per register); the minimum is snapshotted in
+// the even layout.
 //
 // Sweep.  Colours 0..3 in order (faces of one colour have disjoint supports,
 // so their order inside a colour does not matter).  Inside a colour the loop
 // runs over the face columns at run time and unrolls the rows, so register
 // indices stay compile-time constants and the code stays small at any d.
 //
-// Acceptance.  An 8-bit corner signature indexes a per-sweep table of
-// (dE, A): A = T[t][dE] for dE > 0 and A = 0 otherwise, so a move is accepted
-// iff dE <= 0 or u < A.  Draws come four at a time from Philox blocks keyed by
-// (colour, column, row group, sweep, chain); a block is computed only when some
-// lane of the warp has a move with A > 0 in it, since with A = 0 the draw
-// cannot change the outcome.  The table is rebuilt for the next sweep after the
-// warp finishes a sweep, by the warp itself (one copy per warp), so warps
-// never wait for each other.
+// Acceptance.  The corner signature indexes a per-sweep table of (dE, A): A =
+// T[t][dE] for dE > 0 and A = 0 otherwise, so a move is accepted iff dE <= 0
+// or u < A.  Draws come four at a time from Philox blocks keyed by (colour,
+// column, row group, sweep, chain); a block is computed only when some lane of
+// the warp has a move with A > 0 in it, since with A = 0 the draw cannot change
+// the outcome.  The parts of a block's first two rounds that depend only on the
+// chain or the sweep are computed once per chain or sweep.  The table is
+// rebuilt for the next sweep after the warp finishes a sweep, by the warp
+// itself (one copy per warp), so warps never wait for each other.  In the pair
+// path each warp's table sits in its own 4 KB-aligned slot of shared memory,
+// so a table address is the slot base OR'd with the byte offset cut from the
+// pair word.
 //
-// Minimum tracking.  The lowest energy and its rows are recorded at the start
-// and after every colour phase (strict improvement), the rows in shared memory.
+// Minimum tracking.  The lowest energy and its configuration are recorded at
+// the start and after every colour phase (strict improvement), in shared
+// memory.
 #pragma once
 
 #include <type_traits>
@@ -78,6 +93,49 @@ __device__ __forceinline__ uint32_t gather2(uint64_t x) {  // bit 2i -> bit i
   x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
   return (uint32_t)x;
 }
+
+// The annealing draws of one chain: Philox4x32-10 blocks with counter
+// (c0, t, c2, c3), c0 = colour<<16 | column<<8 | row group, t the sweep, (c2,
+// c3) the chain.  Round 0 multiplies c2 (chain-constant) and round 1 multiplies
+// round 0's first output word, which depends only on (chain, sweep); both
+// products and the XORs with constants are taken once per chain or per sweep,
+// leaving one wide multiply in each of the first two rounds per block.  block()
+// returns exactly philox4x32_10(c0, t, c2, c3, K).
+struct SaDraws {
+  uint32_t lo1, B, X1, hi1k;  // per chain
+  uint32_t lo0_1, Y1;         // per sweep
+
+  __device__ __forceinline__ void init(uint32_t c2, uint32_t c3, const PhiloxKeys& K) {
+    const uint64_t p = (uint64_t)c2 * 0xCD9E8D57u;
+    lo1 = (uint32_t)p;
+    B = c3 ^ K.k1[0];
+    X1 = lo1 ^ K.k0[1];
+    hi1k = (uint32_t)(p >> 32) ^ K.k0[0];
+  }
+  __device__ __forceinline__ void sweep(uint32_t t, const PhiloxKeys& K) {
+    const uint64_t q = (uint64_t)(hi1k ^ t) * 0xD2511F53u;  // round 1: c0 = hi(c2 M1) ^ t ^ k0[0]
+    lo0_1 = (uint32_t)q;
+    Y1 = (uint32_t)(q >> 32) ^ K.k1[1];
+  }
+  __device__ __forceinline__ uint4 block(uint32_t c0, const PhiloxKeys& K) const {
+    const uint64_t p0 = (uint64_t)c0 * 0xD2511F53u;        // round 0
+    const uint32_t r0_2 = (uint32_t)(p0 >> 32) ^ B, r0_3 = (uint32_t)p0;
+    const uint64_t p1 = (uint64_t)r0_2 * 0xCD9E8D57u;      // round 1
+    uint32_t a0 = (uint32_t)(p1 >> 32) ^ X1, a1 = (uint32_t)p1, a2 = Y1 ^ r0_3, a3 = lo0_1;
+#pragma unroll
+    for (int r = 2; r < 10; ++r) {
+      const uint64_t q0 = (uint64_t)a0 * 0xD2511F53u;
+      const uint64_t q1 = (uint64_t)a2 * 0xCD9E8D57u;
+      const uint32_t n0 = (uint32_t)(q1 >> 32) ^ a1 ^ K.k0[r];
+      const uint32_t n2 = (uint32_t)(q0 >> 32) ^ a3 ^ K.k1[r];
+      a1 = (uint32_t)q1;
+      a3 = (uint32_t)q0;
+      a0 = n0;
+      a2 = n2;
+    }
+    return make_uint4(a0, a1, a2, a3);
+  }
+};
 
 template <int D, typename Row>
 __device__ __forceinline__ int32_t energy_of(const Row (&R)[D], const int32_t (&W)[4]) {
@@ -155,10 +213,10 @@ __device__ __forceinline__ void store_rows(const Row (&R)[D], uint32_t* __restri
   }
 }
 
-// One colour phase of one sweep.
+// One colour phase of one sweep (row layout, d > 15).
 template <int D, int C, typename Row>
-__device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint2* __restrict__ L, uint32_t t,
-                                             uint32_t c2, uint32_t c3, const PhiloxKeys& K, uint32_t* err) {
+__device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint2* __restrict__ L, const SaDraws& dr,
+                                             const PhiloxKeys& K, uint32_t* err) {
   // Rows of this colour: a = 2j + AOFF; colour 0 ends with the bottom boundary
   // row a = d-1, colour 3 starts with the top boundary row a = -1.
   constexpr int NR = (C == 0 || C == 3) ? (D + 1) / 2 : (D - 1) / 2;
@@ -200,7 +258,7 @@ __device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint
         if (((j + IAOFF) >> 2) == g) need |= e[j].y;
       r[g] = make_uint4(0u, 0u, 0u, 0u);
       if (__any_sync(0xFFFFFFFFu, need != 0u))
-        r[g] = philox4x32_10(((uint32_t)C << 16) | (ib << 8) | (uint32_t)g, t, c2, c3, K);
+        r[g] = dr.block(((uint32_t)C << 16) | (ib << 8) | (uint32_t)g, K);
     }
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
@@ -250,7 +308,7 @@ __device__ __forceinline__ void colour_phase(Row (&R)[D], int32_t& E, const uint
         if (((j + IAOFF) >> 2) == g) need |= e[j].y;
       r[g] = make_uint4(0u, 0u, 0u, 0u);
       if (__any_sync(0xFFFFFFFFu, need != 0u))
-        r[g] = philox4x32_10(((uint32_t)C << 16) | (ibb << 8) | (uint32_t)g, t, c2, c3, K);
+        r[g] = dr.block(((uint32_t)C << 16) | (ibb << 8) | (uint32_t)g, K);
     }
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
@@ -284,6 +342,285 @@ __device__ __forceinline__ void build_lut_warp(uint2* __restrict__ dst, const in
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pair layout (d <= 15).
+// ---------------------------------------------------------------------------
+
+template <int D>
+struct PairShape {
+  static constexpr int H = (D + 1) / 2;          // pair words
+  static constexpr int NW = (4 * D + 31) / 32;   // 32-bit registers per pair word
+};
+
+// Per-warp table of the pair path, indexed by the pair signature: 256 bulk
+// entries (TL | BL << 2 | TR << 4 | BR << 6), 64 for the top boundary (BL | BR
+// << 4), 64 for the bottom (TL | TR << 4), 16 for the left (TR | BR << 2), 16
+// for the right (TL | BL << 2).
+constexpr int kPairTop = 256, kPairBottom = 320, kPairLeft = 384, kPairRight = 400, kPairLut = 416;
+constexpr uint32_t kPairSlot = 4096;  // bytes of one warp's table slot (4 KB aligned)
+
+// Entry of the schedule's rotated signature table for pair index p.
+__device__ __forceinline__ int pair_sig_source(int p) {
+  if (p < kPairTop) {
+    const int TL = p & 3, BL = (p >> 2) & 3, TR = (p >> 4) & 3, BR = (p >> 6) & 3;
+    return TL | (TR << 2) | (BL << 4) | (BR << 6);
+  }
+  if (p < kPairBottom) return sig_base(kTop) + (((p - kPairTop) & 3) | ((((p - kPairTop) >> 4) & 3) << 2));
+  if (p < kPairLeft) return sig_base(kBottom) + (((p - kPairBottom) & 3) | ((((p - kPairBottom) >> 4) & 3) << 2));
+  if (p < kPairRight) return sig_base(kLeft) + (p - kPairLeft);
+  return sig_base(kRight) + (p - kPairRight);
+}
+
+__device__ __forceinline__ uint64_t spread_pairs(uint32_t v) {  // 2-bit field i -> bits 4i, 4i+1
+  uint64_t x = v;
+  x = (x | (x << 16)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x << 8)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x << 2)) & 0x3333333333333333ull;
+  return x;
+}
+
+__device__ __forceinline__ uint32_t gather_pairs(uint64_t x) {  // bits 4i, 4i+1 -> 2-bit field i
+  x &= 0x3333333333333333ull;
+  x = (x | (x >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  x = (x | (x >> 4)) & 0x00FF00FF00FF00FFull;
+  x = (x | (x >> 8)) & 0x0000FFFF0000FFFFull;
+  x = (x | (x >> 16)) & 0x00000000FFFFFFFFull;
+  return (uint32_t)x;
+}
+
+// Rows (two bits per qubit) -> even-layout pair words, and back.  Columns
+// 0..15 of a row fill registers 0 and 1 of its pair word, columns 16..30
+// registers 2 and 3.
+template <int D, typename Row>
+__device__ __forceinline__ void rows_to_pairs(const Row (&R)[D], uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW]) {
+  constexpr int NW = PairShape<D>::NW;
+#pragma unroll
+  for (int j = 0; j < PairShape<D>::H; ++j) {
+    const uint64_t r0 = (uint64_t)R[2 * j], r1 = 2 * j + 1 < D ? (uint64_t)R[2 * j + 1] : 0ull;
+    const uint64_t lo = spread_pairs((uint32_t)r0) | (spread_pairs((uint32_t)r1) << 2);
+    const uint64_t hi = spread_pairs((uint32_t)(r0 >> 32)) | (spread_pairs((uint32_t)(r1 >> 32)) << 2);
+#pragma unroll
+    for (int k = 0; k < NW; ++k) P[j][k] = (uint32_t)((k < 2 ? lo : hi) >> (32 * (k & 1)));
+  }
+}
+template <int D, typename Row>
+__device__ __forceinline__ void pairs_to_rows(const uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW], Row (&R)[D]) {
+  constexpr int NW = PairShape<D>::NW;
+#pragma unroll
+  for (int j = 0; j < PairShape<D>::H; ++j) {
+    const uint64_t lo = (uint64_t)P[j][0] | (NW > 1 ? (uint64_t)P[j][1] << 32 : 0ull);
+    const uint64_t hi = (NW > 2 ? (uint64_t)P[j][2] : 0ull) | (NW > 3 ? (uint64_t)P[j][3] << 32 : 0ull);
+    R[2 * j] = (Row)((uint64_t)gather_pairs(lo) | ((uint64_t)gather_pairs(hi) << 32));
+    if (2 * j + 1 < D) R[2 * j + 1] = (Row)((uint64_t)gather_pairs(lo >> 2) | ((uint64_t)gather_pairs(hi >> 2) << 32));
+  }
+}
+
+// Even layout -> odd layout: Q_j takes row 2j-1 (upper slot of P_{j-1}) as
+// its first row and row 2j (lower slot of P_j) as its second.
+template <int D>
+__device__ __forceinline__ void even_to_odd(uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW]) {
+  constexpr int H = PairShape<D>::H, NW = PairShape<D>::NW;
+#pragma unroll
+  for (int j = H - 1; j >= 0; --j)
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const uint32_t first = j > 0 ? (P[j - 1][k] >> 2) : 0u;
+      P[j][k] = (first & 0x33333333u) | ((P[j][k] << 2) & 0xCCCCCCCCu);
+    }
+}
+// Odd layout -> even layout: P_j takes row 2j (upper slot of Q_j) and row
+// 2j+1 (lower slot of Q_{j+1}).
+template <int D>
+__device__ __forceinline__ void odd_to_even(uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW]) {
+  constexpr int H = PairShape<D>::H, NW = PairShape<D>::NW;
+#pragma unroll
+  for (int j = 0; j < H; ++j)
+#pragma unroll
+    for (int k = 0; k < NW; ++k) {
+      const uint32_t second = j + 1 < H ? (P[j + 1][k] << 2) : 0u;
+      P[j][k] = ((P[j][k] >> 2) & 0x33333333u) | (second & 0xCCCCCCCCu);
+    }
+}
+
+// Where a column's faces sit in their pair words, as kind | register << 4.
+// kIn: inside the register at bit s >= 4; kAt0: at bit 0 of the register (b =
+// 8r); kAcross: bits 28..35 across the register and the next (b = 8r + 7).
+enum PairKind { kIn = 0, kAt0 = 1, kAcross = 2 };
+
+// Byte offset in the warp's table of the signature at bit s (+UP) of w.
+template <int NW, int MODE, int UP>
+__device__ __forceinline__ uint32_t pair_offset(const uint32_t (&w)[NW], uint32_t s, uint32_t mask) {
+  constexpr int KIND = MODE & 15, RG = MODE >> 4;
+  if constexpr (KIND == kIn) return (w[RG] >> (s + UP - 3)) & mask;
+  else if constexpr (KIND == kAt0) return (w[RG] << (3 - UP)) & mask;
+  else return __funnelshift_r(w[RG], w[RG + 1 < NW ? RG + 1 : RG], 28 + UP - 3) & mask;
+}
+
+template <int NW, int MODE>
+__device__ __forceinline__ void pair_flip(uint32_t (&w)[NW], uint32_t m, uint32_t s) {
+  constexpr int KIND = MODE & 15, RG = MODE >> 4;
+  if constexpr (KIND == kIn) {
+    w[RG] ^= m << s;
+  } else if constexpr (KIND == kAt0) {
+    w[RG] ^= m;
+  } else {
+    w[RG] ^= m << 28;
+    w[RG + 1 < NW ? RG + 1 : RG] ^= m >> 4;
+  }
+}
+
+__device__ __forceinline__ uint2 lds_u2(uint32_t addr) {
+  uint2 v;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts_u2(uint32_t addr, uint2 v) {
+  asm volatile("st.shared.v2.u32 [%0], {%1, %2};" ::"r"(addr), "r"(v.x), "r"(v.y));
+}
+
+// Table entry at shared address a inside the slot starting at Lb.
+__device__ __forceinline__ uint2 pair_entry(uint32_t a, uint32_t Lb, uint32_t* err) {
+  return XZZX_CHECK(err, a - Lb <= kPairSlot - 8u && !injected(err, XZZX_DEVERR_BOUNDS)) ? lds_u2(a)
+                                                                                         : make_uint2(0u, 0u);
+}
+
+// One column of faces of colour C at column b (bit s of its register, as MODE
+// says).  Lb: the warp's table slot.
+template <int D, int C, int MODE>
+__device__ __forceinline__ void pair_column(uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW], int32_t& E,
+                                            uint32_t Lb, const SaDraws& dr, const PhiloxKeys& K, int b, uint32_t s,
+                                            uint32_t* err) {
+  constexpr int H = PairShape<D>::H, NW = PairShape<D>::NW;
+  constexpr int NR = (C == 0 || C == 3) ? H : H - 1;
+  constexpr int JOFF = (C == 1) ? 1 : 0;   // colour 1: face row a = 2j+1 is odd pair j+1
+  constexpr int IAOFF = (C == 1) ? 1 : 0;  // ia = (a+1)>>1 = j + IAOFF
+  constexpr int NG = (NR - 1 + IAOFF) / 4 + 1;
+  const uint32_t ib = (uint32_t)(b + 1) >> 1;
+  uint2 e[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    uint32_t a;
+    if (C == 3 && j == 0)  // top boundary (a = -1): second-row slots of odd pair 0
+      a = pair_offset<NW, MODE, 2>(P[0], s, 0x198u) | (Lb + kPairTop * 8);
+    else if (C == 0 && j == NR - 1)  // bottom boundary (a = d-1): first-row slots
+      a = pair_offset<NW, MODE, 0>(P[j], s, 0x198u) | (Lb + kPairBottom * 8);
+    else
+      a = pair_offset<NW, MODE, 0>(P[j + JOFF], s, 0x7F8u) | Lb;
+    e[j] = pair_entry(a, Lb, err);
+  }
+  uint4 r[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    uint32_t need = 0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (((j + IAOFF) >> 2) == g) need |= e[j].y;
+    r[g] = make_uint4(0u, 0u, 0u, 0u);
+    if (__any_sync(0xFFFFFFFFu, need != 0u)) r[g] = dr.block(((uint32_t)C << 16) | (ib << 8) | (uint32_t)g, K);
+  }
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int ia = j + IAOFF;
+    const uint32_t u = lane_of(r[ia >> 2], ia & 3);
+    const int32_t dE = (int32_t)e[j].x;
+    if ((dE <= 0) | (u < e[j].y)) {
+      E += dE;
+      if (C == 3 && j == 0) pair_flip<NW, MODE>(P[0], 0x84u, s);               // Z on BL, X on BR
+      else if (C == 0 && j == NR - 1) pair_flip<NW, MODE>(P[j], 0x12u, s);     // X on TL, Z on TR
+      else pair_flip<NW, MODE>(P[j + JOFF], 0x96u, s);                         // X TL, Z BL, Z TR, X BR
+    }
+  }
+}
+
+// The columns of colour C whose bytes start in register RG of the pair
+// words: b = 8RG at bit 0 (even-b colours), then the columns inside the
+// register, then b = 8RG + 7 across registers RG and RG + 1 (odd-b colours).
+template <int D, int C, int RG>
+__device__ __forceinline__ void pair_register_columns(uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW], int32_t& E,
+                                                      uint32_t Lb, const SaDraws& dr, const PhiloxKeys& K,
+                                                      uint32_t* err) {
+  constexpr int NW = PairShape<D>::NW;
+  if constexpr (RG < NW) {
+    constexpr int PB = C >> 1;
+    constexpr int BMAX = PB + 2 * ((D - 1) / 2 - 1);  // the colour's last bulk column
+    constexpr int B0 = 8 * RG;
+    if constexpr (PB == 0 && B0 <= BMAX) pair_column<D, C, kAt0 | (RG << 4)>(P, E, Lb, dr, K, B0, 0u, err);
+    constexpr int LO = B0 + (PB == 0 ? 2 : 1);
+    constexpr int HI = (B0 + 6 - PB) < BMAX ? (B0 + 6 - PB) : BMAX;
+#pragma unroll 1
+    for (int b = LO; b <= HI; b += 2)
+      pair_column<D, C, kIn | (RG << 4)>(P, E, Lb, dr, K, b, 4u * (uint32_t)(b - B0), err);
+    if constexpr (PB == 1 && B0 + 7 <= BMAX && RG + 1 < NW)
+      pair_column<D, C, kAcross | (RG << 4)>(P, E, Lb, dr, K, B0 + 7, 28u, err);
+    pair_register_columns<D, C, RG + 1>(P, E, Lb, dr, K, err);
+  }
+}
+
+// One colour phase of one sweep (pair layout: even for colours 0 and 2, odd
+// for 1 and 3).
+template <int D, int C>
+__device__ __forceinline__ void pair_phase(uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW], int32_t& E, uint32_t Lb,
+                                           const SaDraws& dr, const PhiloxKeys& K, uint32_t* err) {
+  constexpr int H = PairShape<D>::H;
+  pair_register_columns<D, C, 0>(P, E, Lb, dr, K, err);
+  if constexpr (C == 1 || C == 2) {
+    // Boundary column: right (b = d-1: TL and BL) for colour 1, left (b = -1:
+    // TR and BR) for colour 2, over the bulk rows of the colour.
+    constexpr int NR = H - 1;
+    constexpr int IAOFF = (C == 1) ? 1 : 0;
+    constexpr int JOFF = (C == 1) ? 1 : 0;
+    constexpr int NG = (NR - 1 + IAOFF) / 4 + 1;
+    constexpr uint32_t ibb = (C == 1) ? (uint32_t)(D >> 1) : 0u;
+    constexpr int RB = 4 * (D - 1);
+    constexpr int RW = RB >> 5, RS = RB & 31;
+    uint2 e[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      uint32_t a;
+      if constexpr (C == 1) {
+        if constexpr (RS >= 3) a = ((P[j + JOFF][RW] >> (RS - 3)) & 0x78u) | (Lb + kPairRight * 8);
+        else a = ((P[j + JOFF][RW] << (3 - RS)) & 0x78u) | (Lb + kPairRight * 8);
+      } else {
+        a = ((P[j][0] << 3) & 0x78u) | (Lb + kPairLeft * 8);
+      }
+      e[j] = pair_entry(a, Lb, err);
+    }
+    uint4 r[NG];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      uint32_t need = 0;
+#pragma unroll
+      for (int j = 0; j < NR; ++j)
+        if (((j + IAOFF) >> 2) == g) need |= e[j].y;
+      r[g] = make_uint4(0u, 0u, 0u, 0u);
+      if (__any_sync(0xFFFFFFFFu, need != 0u)) r[g] = dr.block(((uint32_t)C << 16) | (ibb << 8) | (uint32_t)g, K);
+    }
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+      const int ia = j + IAOFF;
+      const uint32_t u = lane_of(r[ia >> 2], ia & 3);
+      const int32_t dE = (int32_t)e[j].x;
+      if ((dE <= 0) | (u < e[j].y)) {
+        E += dE;
+        if constexpr (C == 1) P[j + JOFF][RW] ^= 0x6u << RS;  // X on TL, Z on BL
+        else P[j][0] ^= 0x9u;                                 // Z on TR, X on BR
+      }
+    }
+  }
+}
+
+// Per-sweep pair table of one warp (slot at shared address Lb) from the CTA's
+// static (dE, class) table in pair order.
+__device__ __forceinline__ void build_lut_pair(uint32_t Lb, const int2* __restrict__ sig_pair,
+                                               const uint32_t* __restrict__ Trow, int lane) {
+  for (int idx = lane; idx < kPairLut; idx += 32) {
+    const int2 s = sig_pair[idx];
+    const uint32_t A = s.y >= 0 ? __ldg(&Trow[s.y]) : 0u;
+    sts_u2(Lb + 8u * (uint32_t)idx, make_uint2((uint32_t)s.x, A));
+  }
+}
+
 // Tables a CTA needs: per-sweep thresholds, signature table and qubit weights.
 struct SweepTables {
   const uint32_t* T;
@@ -301,31 +638,44 @@ struct ChainOut {
   uint32_t* final_cfg;
 };
 
-// Shared memory: the static (dE, class) table, one per-sweep table per warp,
-// and the minimum-energy rows of every chain.
+// Shared memory of the row path: the static (dE, class) table, one per-sweep
+// table per warp, and the minimum-energy rows of every chain.
 template <int D, int NT>
-__host__ __device__ constexpr size_t smem_bytes() {
+__host__ __device__ constexpr size_t smem_rows() {
   return kLutN * sizeof(int2) + (size_t)(NT / 32) * kLutN * sizeof(uint2) +
          (size_t)D * NT * sizeof(typename Shape<D>::Row);
 }
 
-// Anneal one chain per thread; every thread of the CTA must call this (it
-// contains barriers).  init: the chain's reference R_i (2w planar words);
-// chain: global chain id (Philox counter); P: coset index of L_P; inactive
-// threads run a copy of a real chain and write nothing.
+// Shared memory of the pair path: 4 KB of alignment slack, one 4 KB table slot
+// per warp, the static table in pair order and the minimum-energy pair words
+// of every chain.
 template <int D, int NT>
-__device__ __forceinline__ void anneal_cta(const uint32_t* __restrict__ init, uint64_t chain, int P, bool active,
-                                           const ChainOut& out, const SweepTables& tab, const PhiloxKeys& K,
-                                           uint8_t* smem) {
+__host__ __device__ constexpr size_t smem_pairs() {
+  return kPairSlot + (size_t)(NT / 32) * kPairSlot + kPairLut * sizeof(int2) +
+         (size_t)PairShape<D>::H * PairShape<D>::NW * NT * sizeof(uint32_t);
+}
+
+// Largest distance annealed in the pair layout (the row layout takes the rest).
+constexpr int kPairMaxD = 15;
+
+template <int D, int NT>
+__host__ __device__ constexpr size_t smem_bytes() {
+  return D <= kPairMaxD ? smem_pairs<D, NT>() : smem_rows<D, NT>();
+}
+
+// Row path (d > 15).  Arguments as anneal_cta.
+template <int D, int NT, int U>
+__device__ __forceinline__ void anneal_cta_rows(const uint32_t* __restrict__ init, uint64_t chain, int P, bool active,
+                                                const ChainOut& out, const SweepTables& tab, const PhiloxKeys& K,
+                                                uint8_t* smem) {
   using Row = typename Shape<D>::Row;
-  constexpr int W = Shape<D>::kW;
   int2* sig_static = reinterpret_cast<int2*>(smem);                                     // [kLutN]
   uint2* lut_all = reinterpret_cast<uint2*>(smem + kLutN * sizeof(int2));               // [NT/32][kLutN]
   Row* best_rows = reinterpret_cast<Row*>(smem + kLutN * sizeof(int2) + (NT / 32) * kLutN * sizeof(uint2));
   const int tid = threadIdx.x, lane = tid & 31;
   uint2* L = lut_all + (tid >> 5) * kLutN;  // this warp's table
-  const uint32_t c2 = (uint32_t)chain;
-  const uint32_t c3 = kTagSA | ((uint32_t)(chain >> 32) << 8);
+  SaDraws dr;
+  dr.init((uint32_t)chain, kTagSA | ((uint32_t)(chain >> 32) << 8), K);
   const int n_sweeps = tab.n_sweeps;
 
   for (int idx = tid; idx < kLutN; idx += NT) sig_static[idx] = __ldg(&tab.sig[idx]);
@@ -351,10 +701,11 @@ __device__ __forceinline__ void anneal_cta(const uint32_t* __restrict__ init, ui
   for (int r = 0; r < D; ++r) best_rows[r * NT + tid] = R[r];
   __syncwarp();
 
+#pragma unroll U
   for (int t = 0; t < n_sweeps; ++t) {
-    const uint32_t tt = (uint32_t)t;
+    dr.sweep((uint32_t)t, K);
 #define XZZX_PHASE(CC)                                                              \
-  colour_phase<D, CC, Row>(R, E, L, tt, c2, c3, K, tab.err);                        \
+  colour_phase<D, CC, Row>(R, E, L, dr, K, tab.err);                                \
   if (E < E_best) {                                                                 \
     E_best = E;                                                                     \
     _Pragma("unroll") for (int r = 0; r < D; ++r) best_rows[r * NT + tid] = R[r];   \
@@ -380,6 +731,110 @@ __device__ __forceinline__ void anneal_cta(const uint32_t* __restrict__ init, ui
     for (int r = 0; r < D; ++r) R[r] = best_rows[r * NT + tid];
     store_rows<D, Row>(R, out.best_cfg);
   }
+}
+
+// Pair path.  Arguments as anneal_cta.
+template <int D, int NT, int U>
+__device__ __forceinline__ void anneal_cta_pairs(const uint32_t* __restrict__ init, uint64_t chain, int P_coset,
+                                                 bool active, const ChainOut& out, const SweepTables& tab,
+                                                 const PhiloxKeys& K, uint8_t* smem) {
+  using Row = typename Shape<D>::Row;
+  constexpr int H = PairShape<D>::H, NW = PairShape<D>::NW;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
+  const uint32_t pad = ((sbase + kPairSlot - 1u) & ~(kPairSlot - 1u)) - sbase;
+  int2* sig_pair = reinterpret_cast<int2*>(smem + pad + (NT / 32) * kPairSlot);               // [kPairLut]
+  uint32_t* best = reinterpret_cast<uint32_t*>(smem + pad + (NT / 32) * kPairSlot + kPairLut * sizeof(int2));
+  const int tid = threadIdx.x, lane = tid & 31;
+  const uint32_t Lb = sbase + pad + (uint32_t)(tid >> 5) * kPairSlot;  // this warp's table slot
+  SaDraws dr;
+  dr.init((uint32_t)chain, kTagSA | ((uint32_t)(chain >> 32) << 8), K);
+  const int n_sweeps = tab.n_sweeps;
+
+  for (int idx = tid; idx < kPairLut; idx += NT) sig_pair[idx] = __ldg(&tab.sig[pair_sig_source(idx)]);
+  __syncthreads();  // the only CTA barrier: warps then sweep independently
+  if (n_sweeps > 0) build_lut_pair(Lb, sig_pair, tab.T, lane);
+
+  Row R[D];
+  load_rows<D, Row>(init, R);
+  // Multiply by L_P: L_X = column 0 (X on even rows, Z on odd rows), L_Z = row 0
+  // (Z on even columns, X on odd columns).
+  if (P_coset == 1 || P_coset == 2) {
+#pragma unroll
+    for (int r = 0; r < D; ++r) R[r] ^= (Row)((r & 1) ? 1u : 2u);
+  }
+  if (P_coset == 2 || P_coset == 3) {
+    const uint64_t mz = 0x9999999999999999ull & ((2 * D >= 64) ? ~0ull : ((1ull << (2 * D)) - 1ull));
+    R[0] ^= (Row)mz;
+  }
+  int32_t W4[4] = {tab.W[0], tab.W[1], tab.W[2], tab.W[3]};
+  int32_t E = energy_of<D, Row>(R, W4);
+  int32_t E_best = E;
+  uint32_t P[H][NW];
+  rows_to_pairs<D, Row>(R, P);
+#pragma unroll
+  for (int j = 0; j < H; ++j)
+#pragma unroll
+    for (int k = 0; k < NW; ++k) best[(j * NW + k) * NT + tid] = P[j][k];
+  __syncwarp();
+
+#pragma unroll U
+  for (int t = 0; t < n_sweeps; ++t) {
+    dr.sweep((uint32_t)t, K);
+#define XZZX_SNAPSHOT                                                                         \
+  if (E < E_best) {                                                                           \
+    E_best = E;                                                                               \
+    _Pragma("unroll") for (int j = 0; j < H; ++j)                                             \
+    _Pragma("unroll") for (int k = 0; k < NW; ++k) best[(j * NW + k) * NT + tid] = P[j][k];   \
+  }
+    pair_phase<D, 0>(P, E, Lb, dr, K, tab.err);
+    XZZX_SNAPSHOT
+    even_to_odd<D>(P);
+    pair_phase<D, 1>(P, E, Lb, dr, K, tab.err);
+    odd_to_even<D>(P);
+    XZZX_SNAPSHOT
+    pair_phase<D, 2>(P, E, Lb, dr, K, tab.err);
+    XZZX_SNAPSHOT
+    even_to_odd<D>(P);
+    pair_phase<D, 3>(P, E, Lb, dr, K, tab.err);
+    odd_to_even<D>(P);
+    XZZX_SNAPSHOT
+#undef XZZX_SNAPSHOT
+    if (t + 1 < n_sweeps) {  // next sweep's thresholds, once every lane is done with these
+      __syncwarp();
+      build_lut_pair(Lb, sig_pair, tab.T + (size_t)(t + 1) * tab.n_classes, lane);
+      __syncwarp();
+    }
+  }
+
+  if (!active) return;
+  *out.best_E = E_best;
+  if (out.final_E) *out.final_E = E;
+  if (out.final_cfg) {
+    pairs_to_rows<D, Row>(P, R);
+    store_rows<D, Row>(R, out.final_cfg);
+  }
+  if (out.best_cfg) {
+#pragma unroll
+    for (int j = 0; j < H; ++j)
+#pragma unroll
+      for (int k = 0; k < NW; ++k) P[j][k] = best[(j * NW + k) * NT + tid];
+    pairs_to_rows<D, Row>(P, R);
+    store_rows<D, Row>(R, out.best_cfg);
+  }
+}
+
+// Anneal one chain per thread; every thread of the CTA must call this (it
+// contains barriers).  init: the chain's reference R_i (2w planar words);
+// chain: global chain id (Philox counter); P: coset index of L_P; inactive
+// threads run a copy of a real chain and write nothing.  smem: smem_bytes<D,
+// NT>() bytes of dynamic shared memory.  U: unroll factor of the sweep loop
+// (a tuning knob; results do not depend on it).
+template <int D, int NT, int U = 1>
+__device__ __forceinline__ void anneal_cta(const uint32_t* __restrict__ init, uint64_t chain, int P, bool active,
+                                           const ChainOut& out, const SweepTables& tab, const PhiloxKeys& K,
+                                           uint8_t* smem) {
+  if constexpr (D <= kPairMaxD) anneal_cta_pairs<D, NT, U>(init, chain, P, active, out, tab, K, smem);
+  else anneal_cta_rows<D, NT, U>(init, chain, P, active, out, tab, K, smem);
 }
 
 }  // namespace core

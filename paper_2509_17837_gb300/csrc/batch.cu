@@ -2,8 +2,8 @@
 // noise classes, schedules and restarts in one run).
 //
 // A plan (build_plan) orders segments by distance, lays their intermediates
-// out in a workspace, and cuts their chains into chunks of kNT chains (one CTA
-// each).  launch_plan then issues, on one stream:
+// out in a workspace, and cuts their chains into chunks of NT chains (one CTA
+// each; NT = 128 or 256, a tuning knob like the sweep unroll of the kernels).  launch_plan then issues, on one stream:
 //   mode 0 (batched): one greedy launch over every (segment, shot, restart
 //          group), one persistent annealing launch whose CTAs pull chunks,
 //          longest first, from an atomic counter, and one decision launch;
@@ -29,16 +29,65 @@
 namespace xzzx {
 namespace batch {
 
-xzzx_status launch_persistent_15(const AnnealLaunch&, int, cudaStream_t);
-xzzx_status launch_persistent_21(const AnnealLaunch&, int, cudaStream_t);
-xzzx_status launch_persistent_31(const AnnealLaunch&, int, cudaStream_t);
-xzzx_status configure_persistent_15();
-xzzx_status configure_persistent_21();
-xzzx_status configure_persistent_31();
-xzzx_status occupancy_persistent_15(int*);
-xzzx_status occupancy_persistent_21(int*);
-xzzx_status occupancy_persistent_31(int*);
-xzzx_status configure_chunk_kernels();
+// Runtime choice of a (chains per CTA, sweep unroll) variant.
+#define XZZX_VARIANTS(CALL)                                                        \
+  if (nt == 128 && unroll == 1) return CALL(128, 1);                                \
+  if (nt == 128 && unroll == 2) return CALL(128, 2);                                \
+  if (nt == 256 && unroll == 1) return CALL(256, 1);                                \
+  if (nt == 256 && unroll == 2) return CALL(256, 2);                                \
+  return fail(XZZX_EINVAL, "chains per CTA must be 128 or 256 and sweep unroll 1 or 2");
+
+xzzx_status launch_chunks(int d, int nt, int unroll, const AnnealLaunch& L, cudaStream_t stream) {
+#define XZZX_CALL(NT, U) launch_chunks_v<NT, U>(d, L, stream)
+  XZZX_VARIANTS(XZZX_CALL)
+#undef XZZX_CALL
+}
+
+xzzx_status occupancy_chunks(int d, int nt, int unroll, int* ctas_per_sm) {
+#define XZZX_CALL(NT, U) occupancy_chunks_v<NT, U>(d, ctas_per_sm)
+  XZZX_VARIANTS(XZZX_CALL)
+#undef XZZX_CALL
+}
+
+static xzzx_status configure_chunk_kernels(int nt, int unroll) {
+#define XZZX_CALL(NT, U) configure_chunks_v<NT, U>()
+  XZZX_VARIANTS(XZZX_CALL)
+#undef XZZX_CALL
+}
+
+static xzzx_status launch_persistent(int dmax, int nt, int unroll, const AnnealLaunch& L, int grid,
+                                     cudaStream_t stream) {
+  if (dmax <= 15) {
+#define XZZX_CALL(NT, U) launch_persistent_v<15, NT, U>(L, grid, stream)
+    XZZX_VARIANTS(XZZX_CALL)
+#undef XZZX_CALL
+  }
+  if (dmax <= 21) {
+#define XZZX_CALL(NT, U) launch_persistent_v<21, NT, U>(L, grid, stream)
+    XZZX_VARIANTS(XZZX_CALL)
+#undef XZZX_CALL
+  }
+#define XZZX_CALL(NT, U) launch_persistent_v<31, NT, U>(L, grid, stream)
+  XZZX_VARIANTS(XZZX_CALL)
+#undef XZZX_CALL
+}
+
+static xzzx_status configure_persistent(int dmax, int nt, int unroll, int* ctas_per_sm) {
+  if (dmax <= 15) {
+#define XZZX_CALL(NT, U) configure_persistent_v<15, NT, U>(ctas_per_sm)
+    XZZX_VARIANTS(XZZX_CALL)
+#undef XZZX_CALL
+  }
+  if (dmax <= 21) {
+#define XZZX_CALL(NT, U) configure_persistent_v<21, NT, U>(ctas_per_sm)
+    XZZX_VARIANTS(XZZX_CALL)
+#undef XZZX_CALL
+  }
+#define XZZX_CALL(NT, U) configure_persistent_v<31, NT, U>(ctas_per_sm)
+  XZZX_VARIANTS(XZZX_CALL)
+#undef XZZX_CALL
+}
+#undef XZZX_VARIANTS
 
 namespace {
 
@@ -142,8 +191,11 @@ AnnealLaunch anneal_launch(const PlanDev& d, const PhiloxKeys& K, const ChunkDev
 
 }  // namespace
 
-xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int order_policy, char* ws_base, Plan& P) {
+xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int order_policy, char* ws_base, Plan& P,
+                       int nt, int unroll) {
   if (n_segs < 1 || !segs) return fail(XZZX_EINVAL, "need at least one segment");
+  if ((nt != 128 && nt != 256) || (unroll != 1 && unroll != 2))
+    return fail(XZZX_EINVAL, "chains per CTA must be 128 or 256 and sweep unroll 1 or 2");
   std::vector<int> order(n_segs);
   std::iota(order.begin(), order.end(), 0);
   for (int i = 0; i < n_segs; ++i) {
@@ -170,6 +222,8 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return segs[x].code->d < segs[y].code->d; });
 
   P = Plan();
+  P.nt = nt;
+  P.unroll = unroll;
   P.segs.resize(n_segs);
   P.cta_prefix.assign(n_segs + 1, 0);
   P.shot_prefix.assign(n_segs + 1, 0);
@@ -211,12 +265,12 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
     P.dmax = std::max(P.dmax, s.code->d);
     const int64_t nch = (int64_t)s.n_shots * s.restarts * 4;
     if (nch > 0x7FFFFFFFll) return fail(XZZX_EINVAL, "segment too large");
-    for (int64_t c = 0; c < nch; c += kNT) {
+    for (int64_t c = 0; c < nch; c += nt) {
       ChunkDev ch;
       ch.seg = j;
       ch.d = s.code->d;
       ch.first_chain = (int)c;
-      ch.n_chains = (int)std::min<int64_t>(kNT, nch - c);
+      ch.n_chains = (int)std::min<int64_t>(nt, nch - c);
       ch.T = s.sched->d_T;
       ch.sig = s.sched->d_sig;
       ch.n_sweeps = s.sched->n_sweeps;
@@ -297,19 +351,10 @@ void pack_descriptors(const Plan& p, char* blob) {
   std::memcpy(blob + L.chain, p.chain_prefix.data(), sizeof(int64_t) * p.chain_prefix.size());
 }
 
-xzzx_status configure_plan_kernels(int dmax, int* ctas_per_sm) {
-  xzzx_status st = configure_chunk_kernels();
+xzzx_status configure_plan_kernels(int dmax, int nt, int unroll, int* ctas_per_sm) {
+  xzzx_status st = configure_chunk_kernels(nt, unroll);
   if (st) return st;
-  if (dmax <= 15) {
-    if ((st = configure_persistent_15())) return st;
-    return occupancy_persistent_15(ctas_per_sm);
-  }
-  if (dmax <= 21) {
-    if ((st = configure_persistent_21())) return st;
-    return occupancy_persistent_21(ctas_per_sm);
-  }
-  if ((st = configure_persistent_31())) return st;
-  return occupancy_persistent_31(ctas_per_sm);
+  return configure_persistent(dmax, nt, unroll, ctas_per_sm);
 }
 
 xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, int grid, int mode,
@@ -323,10 +368,7 @@ xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, in
       XZZX_CUDA_TRY(cudaMemsetAsync(d.head, 0, sizeof(int), stream));
       const AnnealLaunch L = anneal_launch(d, K, d.lpt, 0, n_chunks);
       const int g = std::max(1, std::min(grid, n_chunks));
-      if (p.dmax <= 15) st = launch_persistent_15(L, g, stream);
-      else if (p.dmax <= 21) st = launch_persistent_21(L, g, stream);
-      else st = launch_persistent_31(L, g, stream);
-      if (st) return st;
+      if ((st = launch_persistent(p.dmax, p.nt, p.unroll, L, g, stream))) return st;
     }
     return run_reduce(p, d, 0, p.total_shots, stream);
   }
@@ -343,8 +385,8 @@ xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, in
       W.chain0 = p.chain_prefix[r.seg_begin];
       W.n_chains = p.chain_prefix[r.seg_end] - p.chain_prefix[r.seg_begin];
       if ((st = launch_warp_chains(r.d, W, stream))) return st;
-    } else if ((st = launch_chunks(r.d, anneal_launch(d, K, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin),
-                                   stream))) {
+    } else if ((st = launch_chunks(r.d, p.nt, p.unroll,
+                                   anneal_launch(d, K, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin), stream))) {
       return st;
     }
     if ((st = run_reduce(p, d, p.shot_prefix[r.seg_begin], p.shot_prefix[r.seg_end] - p.shot_prefix[r.seg_begin],
@@ -407,8 +449,8 @@ xzzx_status launch_concurrent(xzzx_batch* b, cudaStream_t stream) {
   for (size_t k = 0; k < n; ++k) {
     const DistanceRange& r = p.ranges[n - 1 - k];  // ranges ascend in d
     XZZX_CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->fork, 0));
-    if ((st = launch_chunks(r.d, anneal_launch(d, b->keys, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin),
-                            b->side[k])))
+    if ((st = launch_chunks(r.d, p.nt, p.unroll,
+                            anneal_launch(d, b->keys, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin), b->side[k])))
       return st;
     XZZX_CUDA_TRY(cudaEventRecord(b->done[k], b->side[k]));
     XZZX_CUDA_TRY(cudaStreamWaitEvent(stream, b->done[k], 0));
@@ -434,8 +476,10 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
   *out = nullptr;
   int device = -1;
   XZZX_CUDA_TRY(cudaGetDevice(&device));
+  const int nt = (cfg && cfg->chains_per_cta) ? cfg->chains_per_cta : kNT;
+  const int unroll = (cfg && cfg->sweep_unroll) ? cfg->sweep_unroll : 1;
   Plan sizing;
-  xzzx_status st = build_plan(segs, n_segs, device, cfg ? cfg->order : 0, nullptr, sizing);
+  xzzx_status st = build_plan(segs, n_segs, device, cfg ? cfg->order : 0, nullptr, sizing, nt, unroll);
   if (st) return st;
   xzzx_batch* b = new (std::nothrow) xzzx_batch();
   if (!b) return fail(XZZX_ENOMEM, "host allocation");
@@ -448,7 +492,7 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
     return cuda_fail(e, "xzzx_batch_create allocation");
   }
   char* base = (char*)b->dev_block;
-  if ((st = build_plan(segs, n_segs, device, cfg ? cfg->order : 0, base + desc, b->plan))) {
+  if ((st = build_plan(segs, n_segs, device, cfg ? cfg->order : 0, base + desc, b->plan, nt, unroll))) {
     free_batch(b);
     return st;
   }
@@ -461,7 +505,7 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
     return cuda_fail(e, "xzzx_batch_create upload");
   }
   int per_sm = 0, n_sm = 0;
-  if ((st = configure_plan_kernels(b->plan.dmax, &per_sm))) {
+  if ((st = configure_plan_kernels(b->plan.dmax, nt, unroll, &per_sm))) {
     free_batch(b);
     return st;
   }
@@ -533,6 +577,8 @@ xzzx_status xzzx_batch_get_info(const xzzx_batch* b, xzzx_batch_info* out) {
   out->workspace_bytes = b->plan.workspace_bytes;
   out->move_attempts = b->plan.attempts;
   out->total_shots = b->plan.total_shots;
+  out->chains_per_cta = b->plan.nt;
+  out->sweep_unroll = b->plan.unroll;
   return XZZX_OK;
 }
 

@@ -1,11 +1,12 @@
-// Batched annealing kernels: a chunk of kNT chains of one segment per CTA.
+// Batched annealing kernels: a chunk of NT chains of one segment per CTA.
 //
-// anneal_chunks_kernel<D>: one CTA per chunk of distance D (the plain,
-// one-launch-per-distance form).  anneal_persistent_kernel<DMAX>: a grid sized
-// to the GPU whose CTAs pull chunk indices from a global atomic counter and
-// run each chunk with the distance-templated core, so distances up to DMAX
-// share one launch.  Both call core::anneal_cta with the same chain ids as
-// xzzx_anneal, so results are identical to per-segment calls.
+// anneal_chunks_kernel<D, NT, U>: one CTA per chunk of distance D (the plain,
+// one-launch-per-distance form).  anneal_persistent_kernel<DMAX, NT, U>: a
+// grid sized to the GPU whose CTAs pull chunk indices from a global atomic
+// counter and run each chunk with the distance-templated core, so distances
+// up to DMAX share one launch.  NT (chains per CTA) and U (sweep-loop unroll)
+// are tuning knobs.  Every form calls core::anneal_cta with the same chain ids
+// as xzzx_anneal, so results are identical to per-segment calls.
 #pragma once
 
 #include "anneal_core.cuh"
@@ -14,7 +15,17 @@
 namespace xzzx {
 namespace batch {
 
-template <int D>
+// CTAs per SM the register allocation is sized for: 1024 threads (64
+// registers) on the pair path; three 128-thread CTAs (170 registers) on the
+// wider row path, whose d = 17..31 state takes about 166.  A persistent kernel
+// takes the bound of its largest distance, so its small-distance chunks do not
+// inflate the allocation of the whole launch.
+template <int D, int NT>
+constexpr int min_blocks() {
+  return D <= core::kPairMaxD ? 1024 / NT : (NT == 128 ? 3 : 1);
+}
+
+template <int D, int NT, int U>
 __device__ __forceinline__ void run_chunk(const ChunkDev& ch, const SegDev& sg, const PhiloxKeys& K, uint8_t* smem) {
   constexpr int W = core::Shape<D>::kW;
   const int tid = threadIdx.x;
@@ -33,30 +44,31 @@ __device__ __forceinline__ void run_chunk(const ChunkDev& ch, const SegDev& sg, 
   out.best_cfg = nullptr;
   out.final_E = nullptr;
   out.final_cfg = nullptr;
-  core::anneal_cta<D, kNT>(sg.init + (size_t)(c >> 2) * 2 * W, chain, (int)(c & 3), active, out, tab, K, smem);
+  core::anneal_cta<D, NT, U>(sg.init + (size_t)(c >> 2) * 2 * W, chain, (int)(c & 3), active, out, tab, K, smem);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kNT) anneal_chunks_kernel(const __grid_constant__ AnnealLaunch L) {
+template <int D, int NT, int U>
+__global__ void __launch_bounds__(NT, (min_blocks<D, NT>())) anneal_chunks_kernel(const __grid_constant__ AnnealLaunch L) {
   extern __shared__ __align__(16) uint8_t smem[];
   const ChunkDev ch = L.chunks[L.chunk0 + blockIdx.x];
-  run_chunk<D>(ch, L.segs[ch.seg], L.keys, smem);
+  run_chunk<D, NT, U>(ch, L.segs[ch.seg], L.keys, smem);
 }
 
-template <int D, int DMAX>
+template <int D, int DMAX, int NT, int U>
 __device__ __forceinline__ void dispatch_chunk(const ChunkDev& ch, const SegDev& sg, const PhiloxKeys& K,
                                                uint8_t* smem) {
   if constexpr (D <= DMAX) {
     if (ch.d == D) {
-      run_chunk<D>(ch, sg, K, smem);
+      run_chunk<D, NT, U>(ch, sg, K, smem);
       return;
     }
-    dispatch_chunk<D + 2, DMAX>(ch, sg, K, smem);
+    dispatch_chunk<D + 2, DMAX, NT, U>(ch, sg, K, smem);
   }
 }
 
-template <int DMAX>
-__global__ void __launch_bounds__(kNT) anneal_persistent_kernel(const __grid_constant__ AnnealLaunch L) {
+template <int DMAX, int NT, int U>
+__global__ void __launch_bounds__(NT, (min_blocks<DMAX, NT>())) anneal_persistent_kernel(
+    const __grid_constant__ AnnealLaunch L) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_next;
   for (;;) {
@@ -66,13 +78,20 @@ __global__ void __launch_bounds__(kNT) anneal_persistent_kernel(const __grid_con
     __syncthreads();
     if (k >= L.n_chunks) break;
     const ChunkDev ch = L.chunks[L.chunk0 + k];
-    dispatch_chunk<3, DMAX>(ch, L.segs[ch.seg], L.keys, smem);
+    dispatch_chunk<3, DMAX, NT, U>(ch, L.segs[ch.seg], L.keys, smem);
   }
 }
 
-template <int DMAX>
+// The largest shared memory of any distance the persistent kernel runs.
+template <int DMAX, int NT, int D = 3>
 constexpr size_t persistent_smem() {
-  return core::smem_bytes<DMAX, kNT>();
+  if constexpr (D > DMAX) {
+    return 0;
+  } else {
+    constexpr size_t here = core::smem_bytes<D, NT>();
+    constexpr size_t rest = persistent_smem<DMAX, NT, D + 2>();
+    return here > rest ? here : rest;
+  }
 }
 
 }  // namespace batch

@@ -1,0 +1,8 @@
+// Chunk kernels of the batch: 128 chains per CTA, sweep loop unrolled 1x.
+#include "batch_chunks.cuh"
+
+namespace xzzx {
+namespace batch {
+XZZX_CHUNK_VARIANT(128, 1)
+}  // namespace batch
+}  // namespace xzzx

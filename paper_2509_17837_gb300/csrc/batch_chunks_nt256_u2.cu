@@ -1,0 +1,8 @@
+// Chunk kernels of the batch: 256 chains per CTA, sweep loop unrolled 2x.
+#include "batch_chunks.cuh"
+
+namespace xzzx {
+namespace batch {
+XZZX_CHUNK_VARIANT(256, 2)
+}  // namespace batch
+}  // namespace xzzx

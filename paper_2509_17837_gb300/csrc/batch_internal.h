@@ -8,7 +8,7 @@
 namespace xzzx {
 namespace batch {
 
-constexpr int kNT = 128;  // chains per CTA in every batched anneal launch
+constexpr int kNT = 128;  // default chains per CTA of the batched anneal launches (128 or 256)
 
 // One homogeneous segment of a batch, as the kernels see it.
 struct SegDev {
@@ -32,7 +32,8 @@ struct SegDev {
   int32_t W[4];
 };
 
-// kNT consecutive chains of one segment (one CTA's work).
+// Up to NT (the plan's chains per CTA) consecutive chains of one segment (one
+// CTA's work).
 struct ChunkDev {
   int seg, d, first_chain, n_chains;
   const uint32_t* T;
@@ -59,6 +60,8 @@ struct DistanceRange {
 // per-distance ranges.  Segment workspace pointers are assigned from a device
 // base address given to build_plan.
 struct Plan {
+  int nt = kNT;     // chains per CTA (chunk size): 128 or 256
+  int unroll = 1;   // sweep-loop unroll of the annealing kernels: 1 or 2
   std::vector<SegDev> segs;
   std::vector<ChunkDev> lpt, byd;
   std::vector<int64_t> cta_prefix, shot_prefix, chain_prefix;
@@ -81,8 +84,10 @@ struct PlanDev {
 };
 
 // Validate segments and build host images; workspace pointers start at
-// ws_base (may be null to size only).  order: 0 = longest chunks first.
-xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int order, char* ws_base, Plan& out);
+// ws_base (may be null to size only).  order: 0 = longest chunks first.  nt:
+// chains per CTA (128 or 256), unroll: sweep-loop unroll (1 or 2).
+xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int order, char* ws_base, Plan& out,
+                       int nt = kNT, int unroll = 1);
 // Bytes of the descriptor blob and the layout of PlanDev inside it.
 size_t descriptor_bytes(const Plan& p);
 PlanDev descriptor_layout(const Plan& p, char* dev_base);
@@ -91,12 +96,26 @@ void pack_descriptors(const Plan& p, char* host_blob);
 // 2: one launch per distance with one warp per chain).
 xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, int grid, int mode,
                         cudaStream_t stream);
-xzzx_status configure_plan_kernels(int dmax, int* ctas_per_sm);
+// Configure the chunk kernels of (nt, unroll) and the persistent kernel of
+// dmax's distance class; its resident CTAs per SM go to *ctas_per_sm.
+xzzx_status configure_plan_kernels(int dmax, int nt, int unroll, int* ctas_per_sm);
 
 // Per-distance chunk kernel (one CTA per chunk).
-xzzx_status launch_chunks(int d, const AnnealLaunch& L, cudaStream_t stream);
+xzzx_status launch_chunks(int d, int nt, int unroll, const AnnealLaunch& L, cudaStream_t stream);
 // Resident CTAs per SM of the distance-d chunk kernel (configured first).
-xzzx_status occupancy_chunks(int d, int* ctas_per_sm);
+xzzx_status occupancy_chunks(int d, int nt, int unroll, int* ctas_per_sm);
+
+// The variants, instantiated in batch_chunks_nt*_u*.cu and batch_persist*.cu.
+template <int NT, int U>
+xzzx_status launch_chunks_v(int d, const AnnealLaunch& L, cudaStream_t stream);
+template <int NT, int U>
+xzzx_status configure_chunks_v();
+template <int NT, int U>
+xzzx_status occupancy_chunks_v(int d, int* ctas_per_sm);
+template <int DMAX, int NT, int U>
+xzzx_status launch_persistent_v(const AnnealLaunch& L, int grid, cudaStream_t stream);
+template <int DMAX, int NT, int U>
+xzzx_status configure_persistent_v(int* ctas_per_sm);
 
 // Per-distance warp-per-chain kernel over the chains [chain0, chain0 + n).
 struct WarpLaunch {

@@ -421,8 +421,8 @@ xzzx_status xzzx_serve_start(xzzx_server* sv) {
   sv->regs_total = (int64_t)regs_per_sm * sv->n_sm * (sv->cfg.resident_waves > 0 ? sv->cfg.resident_waves : 2);
   for (Class& c : sv->classes) {
     int per_sm = 0;
-    if ((st = batch::configure_plan_kernels(c.d, &per_sm))) return st;
-    if ((st = batch::occupancy_chunks(c.d, &per_sm))) return st;
+    if ((st = batch::configure_plan_kernels(c.d, batch::kNT, 1, &per_sm))) return st;
+    if ((st = batch::occupancy_chunks(c.d, batch::kNT, 1, &per_sm))) return st;
     if (per_sm < 1) per_sm = 1;
     const int64_t ctas = (4 * (int64_t)sv->cfg.restarts + batch::kNT - 1) / batch::kNT;
     c.regs = ctas * (regs_per_sm / per_sm);

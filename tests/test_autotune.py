@@ -1,7 +1,7 @@
 """CPU checks of the batch autotuner's logic with a fake batch: it times every
-candidate, picks the fastest (mode, ctas_per_sm, order), caches the choice by
-GPU and batch shape, and serves a repeated shape from the cache without
-timing again."""
+candidate, picks the fastest (mode, ctas_per_sm, order, chains_per_cta,
+sweep_unroll), caches the choice by GPU and batch shape, and serves a
+repeated shape from the cache without timing again."""
 import time
 from types import SimpleNamespace
 
@@ -9,12 +9,12 @@ from paper_2509_17837_gb300 import autotune
 
 
 class FakeBatch:
-    def __init__(self, cps, order, log, cost):
-        self.cps, self.order, self.log, self.cost = cps, order, log, cost
+    def __init__(self, cps, order, nt, unroll, log, cost):
+        self.knobs, self.log, self.cost = (cps, order, nt, unroll), log, cost
 
     def run(self, mode, stream):
-        self.log.append((mode, self.cps, self.order))
-        time.sleep(self.cost(mode, self.cps, self.order))
+        self.log.append((mode,) + self.knobs)
+        time.sleep(self.cost((mode,) + self.knobs))
 
     def close(self):
         pass
@@ -28,12 +28,14 @@ def segments(shots):
 
 def test_picks_fastest_and_caches(tmp_path):
     log = []
-    cost = lambda mode, cps, order: 0.002 if (mode, cps, order) == (1, 0, 0) else 0.006
-    make = lambda cps, order: FakeBatch(cps, order, log, cost)
+    fastest = (1, 0, 0, 256, 2)
+    assert fastest in autotune.DEFAULT_CANDIDATES
+    cost = lambda cand: 0.002 if cand == fastest else 0.004
+    make = lambda cps, order, nt, unroll: FakeBatch(cps, order, nt, unroll, log, cost)
     kw = dict(cache_path=str(tmp_path / "cache.json"), device_name="fake-gpu", stream=None, sync=lambda: None)
     cfg, timings = autotune.tune(make, segments(100), **kw)
-    assert cfg == (1, 0, 0)
-    assert set(timings) == {"%d,%d,%d" % c for c in autotune.DEFAULT_CANDIDATES}
+    assert cfg == fastest
+    assert set(timings) == {",".join(str(x) for x in c) for c in autotune.DEFAULT_CANDIDATES}
     assert {c for c in log} == set(autotune.DEFAULT_CANDIDATES)       # every candidate ran
     n = len(log)
     cfg2, _ = autotune.tune(make, segments(100), **kw)                  # same shape: from the cache

@@ -139,3 +139,25 @@ def test_batch_rejects_bad_segments(env):
     segs[1]["restarts"] = 0
     with pytest.raises(XzzxError):
         X.Batch(segs, 1)
+
+
+@pytest.mark.parametrize("nt,unroll", [(128, 1), (128, 2), (256, 1), (256, 2)])
+def test_batch_tuning_variants_identical(env, nt, unroll):
+    """Every (chains per CTA, sweep unroll) variant of the batched annealing
+    kernels decodes bit-identically to per-segment xzzx_decode_batch, in the
+    persistent, per-distance and concurrent forms."""
+    X, torch = env
+    seed = 0x7A11
+    segs = make_segments(X, torch, seed)
+    refs = reference_outputs(X, torch, segs, seed)
+    b = X.Batch(segs, seed, chains_per_cta=nt, sweep_unroll=unroll)
+    info = b.info()
+    assert info["chains_per_cta"] == nt and info["sweep_unroll"] == unroll
+    for mode in (0, 1, 3):
+        for o in b.outputs:
+            o["cls"].fill_(9)
+        b.run(mode)
+        torch.cuda.synchronize()
+        assert_same(b.outputs, refs)
+    with pytest.raises(X.XzzxError):
+        X.Batch(segs, seed, chains_per_cta=64)
