@@ -381,14 +381,15 @@ def run_uneven(args):
     def form(mode, cps, order, nt, u):
         """A batch in one of the forms, and the call that runs it (modes 0 and 3
         as captured graphs)."""
-        b = X.Batch(segs, seed, ctas_per_sm=cps, order=order, graph_mode=3 if mode == 3 else 0,
+        b = X.Batch(segs, seed, ctas_per_sm=cps, order=order, graph_mode=mode if mode in (3, 4) else 0,
                     chains_per_cta=nt, sweep_unroll=u)
-        run = (lambda: b.run_graph(stream)) if mode in (0, 3) else (lambda: b.run(mode, stream))
+        run = (lambda: b.run_graph(stream)) if mode in (0, 3, 4) else (lambda: b.run(mode, stream))
         return b, run
 
     sampler = ClockSampler(args.clocks_csv, dev)
     sampler.start()
-    forms = {"tuned": cfg, "persistent": best_of((0,)), "concurrent": best_of((3,)), "plain": (1, 0, 0, 128, 1)}
+    forms = {"tuned": cfg, "persistent": best_of((0,)), "concurrent": best_of((3,)),
+             "class_persistent": best_of((4,)), "plain": (1, 0, 0, 128, 1)}
     ms, outs, info = {}, {}, None
     for name, (mode, cps, order, nt, u) in forms.items():
         b, run = form(mode, cps, order, nt, u)
@@ -422,8 +423,9 @@ def run_uneven(args):
                    "segments": info["n_segments"], "chunks": info["n_chunks"],
                    "tuned_cfg": form_rec("tuned")["cfg"],
                    "modes": "0 persistent (one chain per thread, chunk queue), 1 one launch per distance, 2 per "
-                            "distance with one warp per chain, 3 per-distance launches on forked streams; 0 and 3 "
-                            "replayed as captured CUDA graphs",
+                            "distance with one warp per chain, 3 per-distance launches on forked streams, 4 one "
+                            "persistent launch per distance class on forked streams; 0, 3 and 4 replayed as "
+                            "captured CUDA graphs",
                    "autotune": {"batch_shots": int(sum(int(sg["syndromes"].shape[0]) for sg in tune_segs)),
                                 "timings_s": timings},
                    "l2": "flushed between steps"},

@@ -300,7 +300,7 @@ typedef struct {
 typedef struct {
   int32_t ctas_per_sm;    /* persistent grid = SMs x this; 0 = the occupancy maximum */
   int32_t order;          /* chunk queue: 0 = longest chunks first, 1 = segment order */
-  int32_t graph_mode;     /* the mode xzzx_batch_run_graph captures: 0 or 3 */
+  int32_t graph_mode;     /* the mode xzzx_batch_run_graph captures: 0, 3 or 4 */
   int32_t chains_per_cta; /* chains per CTA of the annealing launches (chunk size): 128 or 256; 0 = 128 */
   int32_t sweep_unroll;   /* unroll of the annealing kernels' sweep loop: 1 or 2; 0 = 1 */
 } xzzx_batch_cfg;
@@ -312,6 +312,7 @@ typedef struct {
   double move_attempts;  /* per run */
   int64_t total_shots;
   int32_t chains_per_cta, sweep_unroll;
+  int32_t n_classes;     /* distance classes present (d <= 15, 17..21, 23..31): mode 4's launches */
 } xzzx_batch_info;
 
 typedef struct xzzx_batch xzzx_batch;
@@ -332,9 +333,12 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
  * annealing kernel on its own stream forked from this one (largest distance
  * first, so the hardware fills one distance's tail with the next one's CTAs),
  * joined back before one decision launch; the batch owns those streams.
- * All modes give identical outputs. */
+ * mode 4: as mode 0, with one persistent launch per distance class (d <= 15,
+ * 17..21, 23..31), each with its own chunk queue and the register allocation
+ * of its class, concurrently on forked streams.  All modes give identical
+ * outputs. */
 xzzx_status xzzx_batch_run(xzzx_batch* b, int mode, void* stream);
-/* cfg->graph_mode (0 or 3) captured into a CUDA graph on the first call (stream must not be the
+/* cfg->graph_mode (0, 3 or 4) captured into a CUDA graph on the first call (stream must not be the
  * legacy default stream), replayed on every call. */
 xzzx_status xzzx_batch_run_graph(xzzx_batch* b, void* stream);
 xzzx_status xzzx_batch_get_info(const xzzx_batch* b, xzzx_batch_info* out);

@@ -240,8 +240,9 @@ class Batch:
     Output tensors (cls, E4, recovery, fail) are allocated per segment and
     exposed as ``self.outputs``.  run(mode): 0 = one persistent launch,
     1 = one launch per distance, 2 = as 1 with one warp per chain, 3 = the
-    distances' own launches concurrently on forked streams.  run_graph
-    replays graph_mode (0 or 3) as a captured CUDA graph.
+    distances' own launches concurrently on forked streams, 4 = one
+    persistent launch per distance class concurrently on forked streams.
+    run_graph replays graph_mode (0, 3 or 4) as a captured CUDA graph.
     """
 
     def __init__(self, segments, seed, ctas_per_sm=0, order=0, graph_mode=0, chains_per_cta=0, sweep_unroll=0):

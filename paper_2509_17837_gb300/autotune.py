@@ -6,7 +6,8 @@ It picks, for a batch shape, by timing short runs:
   0 = one persistent launch, one chain per thread, CTAs pulling chunks of
   chains from a queue; 1 = one launch per distance, one chain per thread;
   2 = one launch per distance, one chain per warp; 3 = each distance's own
-  launch, concurrently on forked streams;
+  launch, concurrently on forked streams; 4 = one persistent launch per
+  distance class, concurrently on forked streams;
 * for mode 0, the persistent grid in CTAs per SM (how many chains are in
   flight per SM; 0 = the occupancy limit) and the order of the chunk queue
   (0 = longest chunks first, 1 = segment order);
@@ -28,7 +29,8 @@ KEY_VERSION = "v3"
 # (mode, ctas_per_sm, order, chains_per_cta, sweep_unroll)
 DEFAULT_CANDIDATES = ([(0, c, o, nt, 1) for c in (0, 2, 4) for o in (0, 1) for nt in (128, 256)] +
                       [(0, 0, 0, nt, 2) for nt in (128, 256)] +
-                      [(m, 0, 0, nt, u) for m in (1, 3) for nt in (128, 256) for u in (1, 2)] + [(2, 0, 0, 128, 1)])
+                      [(m, 0, 0, nt, u) for m in (1, 3) for nt in (128, 256) for u in (1, 2)] + [(2, 0, 0, 128, 1)] +
+                      [(4, c, 0, nt, 1) for c in (0, 2) for nt in (128, 256)])
 
 
 def _load(path):

@@ -55,8 +55,7 @@ static xzzx_status configure_chunk_kernels(int nt, int unroll) {
 #undef XZZX_CALL
 }
 
-static xzzx_status launch_persistent(int dmax, int nt, int unroll, const AnnealLaunch& L, int grid,
-                                     cudaStream_t stream) {
+xzzx_status launch_persistent(int dmax, int nt, int unroll, const AnnealLaunch& L, int grid, cudaStream_t stream) {
   if (dmax <= 15) {
 #define XZZX_CALL(NT, U) launch_persistent_v<15, NT, U>(L, grid, stream)
     XZZX_VARIANTS(XZZX_CALL)
@@ -72,7 +71,7 @@ static xzzx_status launch_persistent(int dmax, int nt, int unroll, const AnnealL
 #undef XZZX_CALL
 }
 
-static xzzx_status configure_persistent(int dmax, int nt, int unroll, int* ctas_per_sm) {
+xzzx_status configure_persistent(int dmax, int nt, int unroll, int* ctas_per_sm) {
   if (dmax <= 15) {
 #define XZZX_CALL(NT, U) configure_persistent_v<15, NT, U>(ctas_per_sm)
     XZZX_VARIANTS(XZZX_CALL)
@@ -178,18 +177,19 @@ xzzx_status run_reduce(const Plan& p, const PlanDev& d, int64_t shot0, int64_t n
   return XZZX_OK;
 }
 
-AnnealLaunch anneal_launch(const PlanDev& d, const PhiloxKeys& K, const ChunkDev* chunks, int chunk0, int n) {
+}  // namespace
+
+AnnealLaunch anneal_launch(const PlanDev& d, const PhiloxKeys& K, const ChunkDev* chunks, int chunk0, int n,
+                           int* head) {
   AnnealLaunch L;
   L.keys = K;
   L.segs = d.segs;
   L.chunks = chunks;
   L.chunk0 = chunk0;
   L.n_chunks = n;
-  L.head = d.head;
+  L.head = head ? head : d.head;
   return L;
 }
-
-}  // namespace
 
 xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int order_policy, char* ws_base, Plan& P,
                        int nt, int unroll) {
@@ -286,10 +286,24 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
   P.workspace_bytes = ws;
   P.byd = chunks;  // grouped by distance already (segments are)
   P.lpt = chunks;
+  auto work = [](const ChunkDev& c) { return (int64_t)c.n_sweeps * (c.d * c.d - 1); };
   if (order_policy == 0)
-    std::stable_sort(P.lpt.begin(), P.lpt.end(), [](const ChunkDev& x, const ChunkDev& y) {
-      return (int64_t)x.n_sweeps * (x.d * x.d - 1) > (int64_t)y.n_sweeps * (y.d * y.d - 1);
-    });
+    std::stable_sort(P.lpt.begin(), P.lpt.end(),
+                     [&](const ChunkDev& x, const ChunkDev& y) { return work(x) > work(y); });
+  P.bycls = chunks;
+  std::stable_sort(P.bycls.begin(), P.bycls.end(), [&](const ChunkDev& x, const ChunkDev& y) {
+    const int cx = class_of(x.d), cy = class_of(y.d);
+    if (cx != cy) return cx < cy;
+    return order_policy == 0 && work(x) > work(y);
+  });
+  for (int c = 0, k = 0; c < kNumClasses; ++c) {
+    ClassRange r;
+    r.cls = c;
+    r.chunk_begin = k;
+    while (k < (int)P.bycls.size() && class_of(P.bycls[k].d) == c) ++k;
+    r.chunk_end = k;
+    if (r.chunk_end > r.chunk_begin) P.classes.push_back(r);
+  }
   for (int j = 0; j < n_segs;) {
     DistanceRange r;
     r.d = segs[order[j]].code->d;
@@ -306,7 +320,7 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
 
 namespace {
 struct BlobLayout {
-  size_t segs, lpt, byd, cta, shot, chain, head, total;
+  size_t segs, lpt, byd, bycls, cta, shot, chain, head, total;
 };
 BlobLayout blob_layout(const Plan& p) {
   BlobLayout L;
@@ -314,11 +328,12 @@ BlobLayout blob_layout(const Plan& p) {
   L.segs = 0;
   L.lpt = align256(L.segs + sizeof(SegDev) * p.segs.size());
   L.byd = align256(L.lpt + sizeof(ChunkDev) * nc);
-  L.cta = align256(L.byd + sizeof(ChunkDev) * nc);
+  L.bycls = align256(L.byd + sizeof(ChunkDev) * nc);
+  L.cta = align256(L.bycls + sizeof(ChunkDev) * nc);
   L.shot = align256(L.cta + sizeof(int64_t) * p.cta_prefix.size());
   L.chain = align256(L.shot + sizeof(int64_t) * p.shot_prefix.size());
   L.head = align256(L.chain + sizeof(int64_t) * p.chain_prefix.size());
-  L.total = align256(L.head + sizeof(int));
+  L.total = align256(L.head + sizeof(int) * (1 + kNumClasses));
   return L;
 }
 }  // namespace
@@ -331,6 +346,7 @@ PlanDev descriptor_layout(const Plan& p, char* base) {
   d.segs = (SegDev*)(base + L.segs);
   d.lpt = (ChunkDev*)(base + L.lpt);
   d.byd = (ChunkDev*)(base + L.byd);
+  d.bycls = (ChunkDev*)(base + L.bycls);
   d.cta_prefix = (int64_t*)(base + L.cta);
   d.shot_prefix = (int64_t*)(base + L.shot);
   d.chain_prefix = (int64_t*)(base + L.chain);
@@ -345,6 +361,7 @@ void pack_descriptors(const Plan& p, char* blob) {
   if (!p.lpt.empty()) {
     std::memcpy(blob + L.lpt, p.lpt.data(), sizeof(ChunkDev) * p.lpt.size());
     std::memcpy(blob + L.byd, p.byd.data(), sizeof(ChunkDev) * p.byd.size());
+    std::memcpy(blob + L.bycls, p.bycls.data(), sizeof(ChunkDev) * p.bycls.size());
   }
   std::memcpy(blob + L.cta, p.cta_prefix.data(), sizeof(int64_t) * p.cta_prefix.size());
   std::memcpy(blob + L.shot, p.shot_prefix.data(), sizeof(int64_t) * p.shot_prefix.size());
@@ -366,7 +383,7 @@ xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, in
     if ((st = run_greedy(p, d, K, 0, p.total_ctas, stream))) return st;
     if (n_chunks > 0) {
       XZZX_CUDA_TRY(cudaMemsetAsync(d.head, 0, sizeof(int), stream));
-      const AnnealLaunch L = anneal_launch(d, K, d.lpt, 0, n_chunks);
+      const AnnealLaunch L = anneal_launch(d, K, d.lpt, 0, n_chunks, nullptr);
       const int g = std::max(1, std::min(grid, n_chunks));
       if ((st = launch_persistent(p.dmax, p.nt, p.unroll, L, g, stream))) return st;
     }
@@ -386,7 +403,7 @@ xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, in
       W.n_chains = p.chain_prefix[r.seg_end] - p.chain_prefix[r.seg_begin];
       if ((st = launch_warp_chains(r.d, W, stream))) return st;
     } else if ((st = launch_chunks(r.d, p.nt, p.unroll,
-                                   anneal_launch(d, K, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin), stream))) {
+                                   anneal_launch(d, K, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin, nullptr), stream))) {
       return st;
     }
     if ((st = run_reduce(p, d, p.shot_prefix[r.seg_begin], p.shot_prefix[r.seg_end] - p.shot_prefix[r.seg_begin],
@@ -409,8 +426,9 @@ struct xzzx_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int graph_mode = 0;
-  // mode 3: one side stream and one completion event per distance, and the
-  // fork event, created on first use
+  int class_grid[xzzx::batch::kNumClasses] = {0, 0, 0};  // mode 4: persistent grid of each class
+  // modes 3 and 4: one side stream and one completion event per distance (or
+  // class), and the fork event, created on first use
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> done;
   cudaEvent_t fork = nullptr;
@@ -427,13 +445,7 @@ void free_batch(xzzx_batch* b) {
   if (b->dev_block) cudaFree(b->dev_block);
   delete b;
 }
-// Mode 3: greedy for all segments on `stream`, each distance's chunk kernel on
-// its own side stream (largest distance first), decisions after the join.
-xzzx_status launch_concurrent(xzzx_batch* b, cudaStream_t stream) {
-  using namespace xzzx::batch;
-  const Plan& p = b->plan;
-  const PlanDev& d = b->dev;
-  const size_t n = p.ranges.size();
+xzzx_status ensure_side_streams(xzzx_batch* b, size_t n) {
   while (b->side.size() < n) {
     cudaStream_t s = nullptr;
     XZZX_CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
@@ -443,14 +455,56 @@ xzzx_status launch_concurrent(xzzx_batch* b, cudaStream_t stream) {
     b->done.push_back(e);
   }
   if (!b->fork) XZZX_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
-  xzzx_status st = run_greedy(p, d, b->keys, 0, p.total_ctas, stream);
+  return XZZX_OK;
+}
+
+// Mode 3: greedy for all segments on `stream`, each distance's chunk kernel on
+// its own side stream (largest distance first), decisions after the join.
+xzzx_status launch_concurrent(xzzx_batch* b, cudaStream_t stream) {
+  using namespace xzzx::batch;
+  const Plan& p = b->plan;
+  const PlanDev& d = b->dev;
+  const size_t n = p.ranges.size();
+  xzzx_status st = ensure_side_streams(b, n);
+  if (st) return st;
+  st = run_greedy(p, d, b->keys, 0, p.total_ctas, stream);
   if (st) return st;
   XZZX_CUDA_TRY(cudaEventRecord(b->fork, stream));
   for (size_t k = 0; k < n; ++k) {
     const DistanceRange& r = p.ranges[n - 1 - k];  // ranges ascend in d
     XZZX_CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->fork, 0));
     if ((st = launch_chunks(r.d, p.nt, p.unroll,
-                            anneal_launch(d, b->keys, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin), b->side[k])))
+                            anneal_launch(d, b->keys, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin, nullptr), b->side[k])))
+      return st;
+    XZZX_CUDA_TRY(cudaEventRecord(b->done[k], b->side[k]));
+    XZZX_CUDA_TRY(cudaStreamWaitEvent(stream, b->done[k], 0));
+  }
+  return run_reduce(p, d, 0, p.total_shots, stream);
+}
+
+// Mode 4: greedy for all segments on `stream`, then one persistent launch per
+// distance class (d <= 15, 17..21, 23..31), each on its own side stream with
+// its own chunk queue (longest first) and the register allocation of its
+// class, largest class first; decisions after the join.  Small-distance chunks
+// so keep their own occupancy while the large ones fill the GPU's tails.
+xzzx_status launch_class_persistent(xzzx_batch* b, cudaStream_t stream) {
+  using namespace xzzx::batch;
+  const Plan& p = b->plan;
+  const PlanDev& d = b->dev;
+  const size_t n = p.classes.size();
+  xzzx_status st = ensure_side_streams(b, n);
+  if (st) return st;
+  if ((st = run_greedy(p, d, b->keys, 0, p.total_ctas, stream))) return st;
+  XZZX_CUDA_TRY(cudaEventRecord(b->fork, stream));
+  for (size_t k = 0; k < n; ++k) {
+    const ClassRange& r = p.classes[n - 1 - k];
+    int* head = d.head + 1 + r.cls;
+    const int n_chunks = r.chunk_end - r.chunk_begin;
+    XZZX_CUDA_TRY(cudaStreamWaitEvent(b->side[k], b->fork, 0));
+    XZZX_CUDA_TRY(cudaMemsetAsync(head, 0, sizeof(int), b->side[k]));
+    const int g = std::max(1, std::min(b->class_grid[r.cls], n_chunks));
+    if ((st = launch_persistent(kClassDmax[r.cls], p.nt, p.unroll,
+                                anneal_launch(d, b->keys, d.bycls, r.chunk_begin, n_chunks, head), g, b->side[k])))
       return st;
     XZZX_CUDA_TRY(cudaEventRecord(b->done[k], b->side[k]));
     XZZX_CUDA_TRY(cudaStreamWaitEvent(stream, b->done[k], 0));
@@ -460,6 +514,7 @@ xzzx_status launch_concurrent(xzzx_batch* b, cudaStream_t stream) {
 
 xzzx_status run_mode(xzzx_batch* b, int mode, cudaStream_t stream) {
   if (mode == 3) return launch_concurrent(b, stream);
+  if (mode == 4) return launch_class_persistent(b, stream);
   return xzzx::batch::launch_plan(b->plan, b->dev, b->keys, b->grid, mode, stream);
 }
 
@@ -517,10 +572,20 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
   if (per_sm < 1) per_sm = 1;
   if (cfg && cfg->ctas_per_sm > 0) per_sm = std::min(per_sm, cfg->ctas_per_sm);
   b->grid = n_sm * per_sm;
+  for (const ClassRange& r : b->plan.classes) {
+    int cls_per_sm = 0;
+    if ((st = configure_persistent(kClassDmax[r.cls], nt, unroll, &cls_per_sm))) {
+      free_batch(b);
+      return st;
+    }
+    if (cls_per_sm < 1) cls_per_sm = 1;
+    if (cfg && cfg->ctas_per_sm > 0) cls_per_sm = std::min(cls_per_sm, cfg->ctas_per_sm);
+    b->class_grid[r.cls] = n_sm * cls_per_sm;
+  }
   b->graph_mode = cfg ? cfg->graph_mode : 0;
-  if (b->graph_mode != 0 && b->graph_mode != 3) {
+  if (b->graph_mode != 0 && b->graph_mode != 3 && b->graph_mode != 4) {
     free_batch(b);
-    return fail(XZZX_EINVAL, "graph_mode must be 0 or 3");
+    return fail(XZZX_EINVAL, "graph_mode must be 0, 3 or 4");
   }
   *out = b;
   return XZZX_OK;
@@ -528,10 +593,10 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
 
 xzzx_status xzzx_batch_run(xzzx_batch* b, int mode, void* stream) {
   if (!b) return fail(XZZX_EINVAL, "batch is NULL");
-  if (mode < 0 || mode > 3)
+  if (mode < 0 || mode > 4)
     return fail(XZZX_EINVAL,
-                "mode must be 0 (batched), 1 (one launch per distance), 2 (one warp per chain) or 3 (concurrent "
-                "per-distance launches)");
+                "mode must be 0 (batched), 1 (one launch per distance), 2 (one warp per chain), 3 (concurrent "
+                "per-distance launches) or 4 (concurrent per-class persistent launches)");
   xzzx_status st = check_device(b->device);
   if (st) return st;
   return run_mode(b, mode, (cudaStream_t)stream);
@@ -573,6 +638,7 @@ xzzx_status xzzx_batch_get_info(const xzzx_batch* b, xzzx_batch_info* out) {
   out->n_distances = (int)b->plan.ranges.size();
   out->persistent_grid = std::min(b->grid, std::max((int)b->plan.lpt.size(), 1));
   out->launches_batched = 3;
+  out->n_classes = (int)b->plan.classes.size();
   out->launches_plain = 3 * (int)b->plan.ranges.size();
   out->workspace_bytes = b->plan.workspace_bytes;
   out->move_attempts = b->plan.attempts;

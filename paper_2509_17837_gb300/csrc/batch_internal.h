@@ -56,6 +56,16 @@ struct DistanceRange {
   int chunk_begin, chunk_end;    // chunks_byd range
 };
 
+// Distance classes of the persistent kernels: d <= 15, 17..21, 23..31.
+constexpr int kNumClasses = 3;
+constexpr int kClassDmax[kNumClasses] = {15, 21, 31};
+inline int class_of(int d) { return d <= 15 ? 0 : (d <= 21 ? 1 : 2); }
+
+struct ClassRange {
+  int cls;                       // index into kClassDmax
+  int chunk_begin, chunk_end;    // chunks_bycls range (longest first within the class)
+};
+
 // Host images of a plan: segment and chunk descriptors, prefix sums and the
 // per-distance ranges.  Segment workspace pointers are assigned from a device
 // base address given to build_plan.
@@ -63,7 +73,8 @@ struct Plan {
   int nt = kNT;     // chains per CTA (chunk size): 128 or 256
   int unroll = 1;   // sweep-loop unroll of the annealing kernels: 1 or 2
   std::vector<SegDev> segs;
-  std::vector<ChunkDev> lpt, byd;
+  std::vector<ChunkDev> lpt, byd, bycls;  // longest first; by distance; by class, longest first
+  std::vector<ClassRange> classes;
   std::vector<int64_t> cta_prefix, shot_prefix, chain_prefix;
   std::vector<DistanceRange> ranges;
   int dmax = 0;
@@ -77,10 +88,11 @@ struct PlanDev {
   SegDev* segs;
   ChunkDev* lpt;
   ChunkDev* byd;
+  ChunkDev* bycls;
   int64_t* cta_prefix;
   int64_t* shot_prefix;
   int64_t* chain_prefix;
-  int* head;
+  int* head;  // 1 + kNumClasses queue heads: mode 0's, then one per class (mode 4)
 };
 
 // Validate segments and build host images; workspace pointers start at
@@ -93,12 +105,19 @@ size_t descriptor_bytes(const Plan& p);
 PlanDev descriptor_layout(const Plan& p, char* dev_base);
 void pack_descriptors(const Plan& p, char* host_blob);
 // Enqueue the decode of a plan (mode 0: batched, 1: one launch per distance,
-// 2: one launch per distance with one warp per chain).
+// 2: one launch per distance with one warp per chain).  Modes 3 and 4 need
+// side streams and are issued by the batch handle.
 xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, int grid, int mode,
                         cudaStream_t stream);
 // Configure the chunk kernels of (nt, unroll) and the persistent kernel of
 // dmax's distance class; its resident CTAs per SM go to *ctas_per_sm.
 xzzx_status configure_plan_kernels(int dmax, int nt, int unroll, int* ctas_per_sm);
+// The persistent kernel of a distance class: configure it (resident CTAs per
+// SM to *ctas_per_sm) and launch it.
+xzzx_status configure_persistent(int dmax, int nt, int unroll, int* ctas_per_sm);
+xzzx_status launch_persistent(int dmax, int nt, int unroll, const AnnealLaunch& L, int grid, cudaStream_t stream);
+AnnealLaunch anneal_launch(const PlanDev& d, const PhiloxKeys& K, const ChunkDev* chunks, int chunk0, int n,
+                           int* head);
 
 // Per-distance chunk kernel (one CTA per chunk).
 xzzx_status launch_chunks(int d, int nt, int unroll, const AnnealLaunch& L, cudaStream_t stream);

@@ -72,7 +72,7 @@ def test_batch_modes_match_per_segment_calls(env):
     info = b.info()
     assert info["n_segments"] == len(SEG_SPECS) and info["n_distances"] == 7
     assert info["launches_batched"] == 3 and info["launches_plain"] == 21
-    for mode in (0, 1, 2, 3, 0, 3):   # second runs reuse the reset queue and the side streams
+    for mode in (0, 1, 2, 3, 4, 0, 3, 4):   # second runs reuse the reset queues and the side streams
         for o in b.outputs:
             for t in o.values():
                 if t is not None:
@@ -90,14 +90,17 @@ def test_batch_modes_match_per_segment_calls(env):
         assert_same(b.outputs, refs)
 
 
-def test_batch_concurrent_mode_graph(env):
-    """Mode 3 (each distance's own launch on forked streams) captured as a
+@pytest.mark.parametrize("graph_mode", [3, 4])
+def test_batch_concurrent_mode_graph(env, graph_mode):
+    """Modes 3 (each distance's own launch on forked streams) and 4 (one
+    persistent launch per distance class on forked streams) captured as a
     CUDA graph and replayed: identical outputs to the per-segment calls."""
     X, torch = env
     seed = 0x3C0C
     segs = make_segments(X, torch, seed)
     refs = reference_outputs(X, torch, segs, seed)
-    b = X.Batch(segs, seed, graph_mode=3)
+    b = X.Batch(segs, seed, graph_mode=graph_mode)
+    assert b.info()["n_classes"] == 2
     s = torch.cuda.Stream()
     for _ in range(3):
         for o in b.outputs:
@@ -153,7 +156,7 @@ def test_batch_tuning_variants_identical(env, nt, unroll):
     b = X.Batch(segs, seed, chains_per_cta=nt, sweep_unroll=unroll)
     info = b.info()
     assert info["chains_per_cta"] == nt and info["sweep_unroll"] == unroll
-    for mode in (0, 1, 3):
+    for mode in (0, 1, 3, 4):
         for o in b.outputs:
             o["cls"].fill_(9)
         b.run(mode)
