@@ -92,7 +92,8 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, path, gpu_index):
-        if not path:
+        self.temporary = not path
+        if self.temporary:
             import tempfile
             fd, path = tempfile.mkstemp(prefix="xzzx_clocks_", suffix=".csv")
             os.close(fd)
@@ -131,6 +132,8 @@ class ClockSampler:
             for nm, v in zip(names, parts[5:9]):
                 if v.lower() == "active":
                     reasons.add(nm)
+        if self.temporary:
+            os.unlink(self.path)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         top = max(sm)
@@ -355,7 +358,7 @@ def run_uneven(args):
     tune_segs = uneven_segments(X, args.uneven_shots, seed, scale_shots=tune_scale)
     cfg, timings = autotune.tune(
         lambda c, o, nt, u: X.Batch(tune_segs, seed, ctas_per_sm=c, order=o, chains_per_cta=nt, sweep_unroll=u),
-        tune_segs, use_cache=False)
+        tune_segs, reps=2, use_cache=False)
     knobs = lambda key: tuple(int(x) for x in key.split(","))
     best_of = lambda modes: knobs(min((k for k in timings if knobs(k)[0] in modes), key=timings.get))
     dev = torch.cuda.current_device()
@@ -605,7 +608,7 @@ def run_large(args):
         "logical_error_rates": [stats.ler_record(p, f, S * args.steps) for p, f in zip(LARGE_PS, fails)],
         "chain_mapping": mapping, "occupancy_sweep": occupancy, "clocks": clocks,
         "roofline": roofline_record(att, clocks, props.multi_processor_count, traffic=None,
-                                    kernel="anneal_kernel<31>")}))
+                                    kernel="anneal_kernel_rows<31>")}))
 
 
 # --------------------------------------------------------------------------- logical error rate curves

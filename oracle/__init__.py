@@ -25,7 +25,7 @@ LINEAR, PAPER_LOG = 0, 1
 INIT_GREEDY, INIT_GREEDY_RANDOM, INIT_BOUNDARY = 0, 1, 2
 ORDER_COLOUR, ORDER_RANDOM_SITE = 0, 1
 EMIN_PER_PHASE, EMIN_PER_ATTEMPT = 0, 1
-BASELINE_ETA, PAPER_ETA = 0, 1
+Y_OVER_XZ_ETA, PAPER_ETA = 0, 1
 PLANAR_ID = 1000
 
 
@@ -116,7 +116,7 @@ def logicals(d):
     return LX, LZ
 
 
-def noise_from_eta(p, eta, convention=BASELINE_ETA):
+def noise_from_eta(p, eta, convention=Y_OVER_XZ_ETA):
     out = np.zeros(3, np.float64)
     _check(lib().orc_noise_from_eta(p, eta, convention, _ptr(out)), "noise_from_eta")
     return tuple(float(x) for x in out)

@@ -14,7 +14,7 @@ from ._lib import (XZZX_ETIMEOUT, BatchCfg, BatchInfo, CodeInfo, Noise, Result, 
                    XzzxError, call, lib)
 
 LINEAR, PAPER_LOG = 0, 1
-CONVENTION_BASELINE, CONVENTION_PAPER = 0, 1
+CONVENTION_Y_OVER_XZ, CONVENTION_PAPER = 0, 1
 LAYOUT_ROTATED, LAYOUT_PLANAR = 0, 1         # xzzx_make_code layouts
 ORDER_COLOUR, ORDER_RANDOM_SITE = 0, 1       # sweep order of xzzx_anneal_variant
 EMIN_PER_PHASE, EMIN_PER_ATTEMPT = 0, 1      # when the minimum is taken
@@ -100,7 +100,7 @@ def make_noise(px, py, pz, scale=1024):
     return n
 
 
-def noise_from_eta(p, eta, convention=CONVENTION_BASELINE, scale=1024):
+def noise_from_eta(p, eta, convention=CONVENTION_Y_OVER_XZ, scale=1024):
     n = Noise()
     call("xzzx_noise_from_eta", p, eta, convention, scale, C.byref(n))
     return n

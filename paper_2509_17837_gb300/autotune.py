@@ -88,11 +88,13 @@ def tune(make_batch, segments, candidates=None, reps=1, use_cache=True, cache_pa
         try:
             b.run(mode, stream)  # warm-up
             sync()
-            t0 = time.perf_counter()
-            for _ in range(reps):
+            best_s = float("inf")
+            for _ in range(reps):  # the fastest of reps runs: robust to one-off interference
+                t0 = time.perf_counter()
                 b.run(mode, stream)
-            sync()
-            timings[",".join(str(x) for x in cand)] = (time.perf_counter() - t0) / reps
+                sync()
+                best_s = min(best_s, time.perf_counter() - t0)
+            timings[",".join(str(x) for x in cand)] = best_s
         finally:
             b.close()
     best = min(timings, key=timings.get)

@@ -25,8 +25,11 @@ struct AnnealArgs {
   uint32_t* err;
 };
 
+// One chain per thread.  The pair path (d <= 15) is bounded to four 256-thread
+// CTAs per SM (64 registers); the row path keeps the compiler's choice for
+// 128-thread CTAs (about 120 registers up to d = 29, 160 at d = 31).
 template <int D>
-__global__ void __launch_bounds__(Shape<D>::kThreads) anneal_kernel(const __grid_constant__ AnnealArgs A) {
+__device__ __forceinline__ void anneal_body(const AnnealArgs& A) {
   constexpr int NT = Shape<D>::kThreads;
   constexpr int W = Shape<D>::kW;
   extern __shared__ __align__(16) uint8_t smem[];
@@ -50,18 +53,32 @@ __global__ void __launch_bounds__(Shape<D>::kThreads) anneal_kernel(const __grid
 }
 
 template <int D>
+__global__ void __launch_bounds__(Shape<D>::kThreads, 4) anneal_kernel(const __grid_constant__ AnnealArgs A) {
+  anneal_body<D>(A);
+}
+template <int D>
+__global__ void __launch_bounds__(Shape<D>::kThreads) anneal_kernel_rows(const __grid_constant__ AnnealArgs A) {
+  anneal_body<D>(A);
+}
+template <int D>
+constexpr auto anneal_kernel_of() {
+  if constexpr (D <= kPairMaxD) return &anneal_kernel<D>;
+  else return &anneal_kernel_rows<D>;
+}
+
+template <int D>
 xzzx_status launch_d(const AnnealArgs& A, cudaStream_t stream) {
   constexpr int NT = Shape<D>::kThreads;
   const size_t smem = smem_bytes<D, NT>();
   static DeviceOnce once;
   xzzx_status st = once.run([&]() -> xzzx_status {
-    XZZX_CUDA_TRY(cudaFuncSetAttribute(anneal_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    XZZX_CUDA_TRY(cudaFuncSetAttribute(anneal_kernel_of<D>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     return XZZX_OK;
   });
   if (st) return st;
   const int64_t grid = (A.n_chains + NT - 1) / NT;
   if (grid > 0x7FFFFFFF) return fail(XZZX_EINVAL, "too many chains for one launch");
-  anneal_kernel<D><<<(unsigned)grid, NT, smem, stream>>>(A);
+  anneal_kernel_of<D>()<<<(unsigned)grid, NT, smem, stream>>>(A);
   XZZX_CUDA_TRY(cudaGetLastError());
   return XZZX_OK;
 }

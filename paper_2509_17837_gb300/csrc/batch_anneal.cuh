@@ -15,16 +15,6 @@
 namespace xzzx {
 namespace batch {
 
-// CTAs per SM the register allocation is sized for: 1024 threads (64
-// registers) on the pair path; three 128-thread CTAs (170 registers) on the
-// wider row path, whose d = 17..31 state takes about 166.  A persistent kernel
-// takes the bound of its largest distance, so its small-distance chunks do not
-// inflate the allocation of the whole launch.
-template <int D, int NT>
-constexpr int min_blocks() {
-  return D <= core::kPairMaxD ? 1024 / NT : (NT == 128 ? 3 : 1);
-}
-
 template <int D, int NT, int U>
 __device__ __forceinline__ void run_chunk(const ChunkDev& ch, const SegDev& sg, const PhiloxKeys& K, uint8_t* smem) {
   constexpr int W = core::Shape<D>::kW;
@@ -47,11 +37,25 @@ __device__ __forceinline__ void run_chunk(const ChunkDev& ch, const SegDev& sg, 
   core::anneal_cta<D, NT, U>(sg.init + (size_t)(c >> 2) * 2 * W, chain, (int)(c & 3), active, out, tab, K, smem);
 }
 
+// Register bounds: kernels on the pair path (d <= 15) are held to 1024
+// threads per SM (64 registers); kernels on the row path keep the compiler's
+// choice for their CTA size.
 template <int D, int NT, int U>
-__global__ void __launch_bounds__(NT, (min_blocks<D, NT>())) anneal_chunks_kernel(const __grid_constant__ AnnealLaunch L) {
+__global__ void __launch_bounds__(NT, (1024 / NT)) anneal_chunks_kernel(const __grid_constant__ AnnealLaunch L) {
   extern __shared__ __align__(16) uint8_t smem[];
   const ChunkDev ch = L.chunks[L.chunk0 + blockIdx.x];
   run_chunk<D, NT, U>(ch, L.segs[ch.seg], L.keys, smem);
+}
+template <int D, int NT, int U>
+__global__ void __launch_bounds__(NT) anneal_chunks_kernel_rows(const __grid_constant__ AnnealLaunch L) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const ChunkDev ch = L.chunks[L.chunk0 + blockIdx.x];
+  run_chunk<D, NT, U>(ch, L.segs[ch.seg], L.keys, smem);
+}
+template <int D, int NT, int U>
+constexpr auto chunks_kernel_of() {
+  if constexpr (D <= core::kPairMaxD) return &anneal_chunks_kernel<D, NT, U>;
+  else return &anneal_chunks_kernel_rows<D, NT, U>;
 }
 
 template <int D, int DMAX, int NT, int U>
@@ -67,8 +71,7 @@ __device__ __forceinline__ void dispatch_chunk(const ChunkDev& ch, const SegDev&
 }
 
 template <int DMAX, int NT, int U>
-__global__ void __launch_bounds__(NT, (min_blocks<DMAX, NT>())) anneal_persistent_kernel(
-    const __grid_constant__ AnnealLaunch L) {
+__device__ __forceinline__ void persistent_body(const AnnealLaunch& L) {
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ int s_next;
   for (;;) {
@@ -80,6 +83,19 @@ __global__ void __launch_bounds__(NT, (min_blocks<DMAX, NT>())) anneal_persisten
     const ChunkDev ch = L.chunks[L.chunk0 + k];
     dispatch_chunk<3, DMAX, NT, U>(ch, L.segs[ch.seg], L.keys, smem);
   }
+}
+template <int DMAX, int NT, int U>
+__global__ void __launch_bounds__(NT, (1024 / NT)) anneal_persistent_kernel(const __grid_constant__ AnnealLaunch L) {
+  persistent_body<DMAX, NT, U>(L);
+}
+template <int DMAX, int NT, int U>
+__global__ void __launch_bounds__(NT) anneal_persistent_kernel_rows(const __grid_constant__ AnnealLaunch L) {
+  persistent_body<DMAX, NT, U>(L);
+}
+template <int DMAX, int NT, int U>
+constexpr auto persistent_kernel_of() {
+  if constexpr (DMAX <= core::kPairMaxD) return &anneal_persistent_kernel<DMAX, NT, U>;
+  else return &anneal_persistent_kernel_rows<DMAX, NT, U>;
 }
 
 // The largest shared memory of any distance the persistent kernel runs.

@@ -13,7 +13,7 @@ template <int D, int NT, int U>
 static xzzx_status chunks_d(const AnnealLaunch& L, cudaStream_t stream) {
   constexpr size_t smem = core::smem_bytes<D, NT>();
   if (L.n_chunks == 0) return XZZX_OK;
-  anneal_chunks_kernel<D, NT, U><<<(unsigned)L.n_chunks, NT, smem, stream>>>(L);
+  chunks_kernel_of<D, NT, U>()<<<(unsigned)L.n_chunks, NT, smem, stream>>>(L);
   XZZX_CUDA_TRY(cudaGetLastError());
   return XZZX_OK;
 }
@@ -22,14 +22,14 @@ template <int D, int NT, int U>
 static xzzx_status configure_chunks_d() {
   constexpr size_t smem = core::smem_bytes<D, NT>();
   XZZX_CUDA_TRY(
-      cudaFuncSetAttribute(anneal_chunks_kernel<D, NT, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      cudaFuncSetAttribute(chunks_kernel_of<D, NT, U>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   return XZZX_OK;
 }
 
 template <int D, int NT, int U>
 static xzzx_status occupancy_chunks_d(int* ctas_per_sm) {
   constexpr size_t smem = core::smem_bytes<D, NT>();
-  XZZX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, anneal_chunks_kernel<D, NT, U>, NT, smem));
+  XZZX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, chunks_kernel_of<D, NT, U>(), NT, smem));
   return XZZX_OK;
 }
 

@@ -11,7 +11,7 @@ namespace batch {
 template <int DMAX, int NT, int U>
 xzzx_status launch_persistent_v(const AnnealLaunch& L, int grid, cudaStream_t stream) {
   constexpr size_t smem = persistent_smem<DMAX, NT>();
-  anneal_persistent_kernel<DMAX, NT, U><<<(unsigned)grid, NT, smem, stream>>>(L);
+  persistent_kernel_of<DMAX, NT, U>()<<<(unsigned)grid, NT, smem, stream>>>(L);
   XZZX_CUDA_TRY(cudaGetLastError());
   return XZZX_OK;
 }
@@ -19,10 +19,10 @@ xzzx_status launch_persistent_v(const AnnealLaunch& L, int grid, cudaStream_t st
 template <int DMAX, int NT, int U>
 xzzx_status configure_persistent_v(int* ctas_per_sm) {
   constexpr size_t smem = persistent_smem<DMAX, NT>();
-  XZZX_CUDA_TRY(cudaFuncSetAttribute(anneal_persistent_kernel<DMAX, NT, U>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  XZZX_CUDA_TRY(cudaFuncSetAttribute(persistent_kernel_of<DMAX, NT, U>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
   XZZX_CUDA_TRY(
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, anneal_persistent_kernel<DMAX, NT, U>, NT, smem));
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, persistent_kernel_of<DMAX, NT, U>(), NT, smem));
   return XZZX_OK;
 }
 

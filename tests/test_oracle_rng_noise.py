@@ -51,7 +51,7 @@ def test_philox_uniform():
 
 
 def test_bias_conventions():
-    px, py, pz = O.noise_from_eta(0.1, 10, O.BASELINE_ETA)
+    px, py, pz = O.noise_from_eta(0.1, 10, O.Y_OVER_XZ_ETA)
     assert math.isclose(py, 0.1 * 10 / 11) and math.isclose(px, 0.1 / 22) and px == pz
     assert math.isclose(px + py + pz, 0.1)
     px, py, pz = O.noise_from_eta(0.3, 1.0, O.PAPER_ETA)   # eta = 1 is depolarizing
