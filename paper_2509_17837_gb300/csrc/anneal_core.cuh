@@ -610,14 +610,28 @@ __device__ __forceinline__ void pair_phase(uint32_t (&P)[PairShape<D>::H][PairSh
   }
 }
 
-// Per-sweep pair table of one warp (slot at shared address Lb) from the CTA's
-// static (dE, class) table in pair order.
+__device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+// Pair table of one warp (slot at shared address Lb) for the first sweep, in
+// full, from the CTA's static (dE, class) table in pair order.
 __device__ __forceinline__ void build_lut_pair(uint32_t Lb, const int2* __restrict__ sig_pair,
                                                const uint32_t* __restrict__ Trow, int lane) {
   for (int idx = lane; idx < kPairLut; idx += 32) {
     const int2 s = sig_pair[idx];
     const uint32_t A = s.y >= 0 ? __ldg(&Trow[s.y]) : 0u;
     sts_u2(Lb + 8u * (uint32_t)idx, make_uint2((uint32_t)s.x, A));
+  }
+}
+
+// Later sweeps only change the thresholds of the entries with dE > 0: upd
+// lists them as index << 16 | class (n_upd entries).
+__device__ __forceinline__ void update_lut_pair(uint32_t Lb, const uint32_t* __restrict__ upd, int n_upd,
+                                                const uint32_t* __restrict__ Trow, int lane) {
+  for (int k = lane; k < n_upd; k += 32) {
+    const uint32_t v = upd[k];
+    sts_u32(Lb + 8u * (v >> 16) + 4u, __ldg(&Trow[v & 0xFFFFu]));
   }
 }
 
@@ -651,7 +665,7 @@ __host__ __device__ constexpr size_t smem_rows() {
 // of every chain.
 template <int D, int NT>
 __host__ __device__ constexpr size_t smem_pairs() {
-  return kPairSlot + (size_t)(NT / 32) * kPairSlot + kPairLut * sizeof(int2) +
+  return kPairSlot + (size_t)(NT / 32) * kPairSlot + kPairLut * sizeof(int2) + kPairLut * sizeof(uint32_t) + 16 +
          (size_t)PairShape<D>::H * PairShape<D>::NW * NT * sizeof(uint32_t);
 }
 
@@ -743,7 +757,9 @@ __device__ __forceinline__ void anneal_cta_pairs(const uint32_t* __restrict__ in
   const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(smem);
   const uint32_t pad = ((sbase + kPairSlot - 1u) & ~(kPairSlot - 1u)) - sbase;
   int2* sig_pair = reinterpret_cast<int2*>(smem + pad + (NT / 32) * kPairSlot);               // [kPairLut]
-  uint32_t* best = reinterpret_cast<uint32_t*>(smem + pad + (NT / 32) * kPairSlot + kPairLut * sizeof(int2));
+  uint32_t* upd = reinterpret_cast<uint32_t*>(sig_pair + kPairLut);                            // [kPairLut]
+  int* n_upd_s = reinterpret_cast<int*>(upd + kPairLut);                                       // [4]
+  uint32_t* best = reinterpret_cast<uint32_t*>(n_upd_s + 4);
   const int tid = threadIdx.x, lane = tid & 31;
   const uint32_t Lb = sbase + pad + (uint32_t)(tid >> 5) * kPairSlot;  // this warp's table slot
   SaDraws dr;
@@ -751,7 +767,20 @@ __device__ __forceinline__ void anneal_cta_pairs(const uint32_t* __restrict__ in
   const int n_sweeps = tab.n_sweeps;
 
   for (int idx = tid; idx < kPairLut; idx += NT) sig_pair[idx] = __ldg(&tab.sig[pair_sig_source(idx)]);
-  __syncthreads();  // the only CTA barrier: warps then sweep independently
+  __syncthreads();
+  if (tid < 32) {  // the entries whose threshold changes from sweep to sweep, in index order
+    int n = 0;
+    for (int base = 0; base < kPairLut; base += 32) {
+      const int idx = base + tid;
+      const int cls = idx < kPairLut ? sig_pair[idx].y : -1;
+      const uint32_t m = __ballot_sync(0xFFFFFFFFu, cls >= 0);
+      if (cls >= 0) upd[n + __popc(m & ((1u << tid) - 1u))] = ((uint32_t)idx << 16) | (uint32_t)cls;
+      n += __popc(m);
+    }
+    if (tid == 0) n_upd_s[0] = n;
+  }
+  __syncthreads();  // the last CTA barrier: warps then sweep independently
+  const int n_upd = n_upd_s[0];
   if (n_sweeps > 0) build_lut_pair(Lb, sig_pair, tab.T, lane);
 
   Row R[D];
@@ -801,7 +830,7 @@ __device__ __forceinline__ void anneal_cta_pairs(const uint32_t* __restrict__ in
 #undef XZZX_SNAPSHOT
     if (t + 1 < n_sweeps) {  // next sweep's thresholds, once every lane is done with these
       __syncwarp();
-      build_lut_pair(Lb, sig_pair, tab.T + (size_t)(t + 1) * tab.n_classes, lane);
+      update_lut_pair(Lb, upd, n_upd, tab.T + (size_t)(t + 1) * tab.n_classes, lane);
       __syncwarp();
     }
   }
