@@ -39,9 +39,12 @@ I_ALG = 30  # integer instructions per move attempt in the algorithmic count
 # clock per SM sub-partition), all lane instructions per attempt
 # (smsp__inst_executed x 32 / attempts) and shared-memory bank conflicts per
 # shared wavefront.
-ANNEAL_DRAM_BYTES_PER_CHAIN = None
-ANNEAL_ALU_INST_PER_ATTEMPT = None
-ANNEAL_MEASURED = None
+ANNEAL_DRAM_BYTES_PER_CHAIN = 8.399872e6 / 1.024e6
+ANNEAL_ALU_INST_PER_ATTEMPT = 12.12
+ANNEAL_MEASURED = {"inst_per_attempt": 20.51, "alu_inst_per_attempt": ANNEAL_ALU_INST_PER_ATTEMPT,
+                   "shared_bank_conflicts_per_wavefront": 1.2654e10 / 2.0863e10,
+                   "source": "ncu capture of one anneal_kernel<11> launch of 4000 shots, "
+                             "profiles/anneal_d11_ncu_full.md"}
 
 
 def workload_config(shots_per_p, world):
