@@ -314,10 +314,13 @@ UNEVEN_ETAS = (1.0, 10.0, 100.0)
 UNEVEN_PS = tuple(round(0.08 + 0.005 * k, 3) for k in range(25))   # [0.08, 0.20] on a 0.005 grid
 
 
-def uneven_segments(X, total_shots, seed, scale_shots=1.0):
+def uneven_segments(X, total_shots, seed, scale_shots=1.0, scale_sweeps=1.0):
     """Shots of distances {5,7,9,13,17,21} in equal numbers; eta and p drawn per
     shot from the seed (p on a 0.005 grid: 75 noise classes per distance);
-    shots bucketed into homogeneous segments with disjoint shot indices."""
+    shots bucketed into homogeneous segments with disjoint shot indices.
+    scale_shots / scale_sweeps shrink the batch for the autotuner: fewer
+    sweeps keep every distance's chunk count, so the waves and tails the forms
+    differ on keep their shape while each run is shorter."""
     import numpy as np
     rng = np.random.default_rng(seed)
     per_d = total_shots // len(UNEVEN_DS)
@@ -336,7 +339,7 @@ def uneven_segments(X, total_shots, seed, scale_shots=1.0):
             noise = X.noise_from_eta(p, eta)
             key = (d, eta, p)
             if key not in scheds:
-                scheds[key] = X.Schedule(noise, UNEVEN_N[d], BETA0, BETA1)
+                scheds[key] = X.Schedule(noise, max(1, int(round(UNEVEN_N[d] * scale_sweeps))), BETA0, BETA1)
             err, syn = X.sample_errors(codes[d], noise, seed, shot_base, n)
             segs.append(dict(code=codes[d], noise=noise, sched=scheds[key], shot0=shot_base, syndromes=syn,
                              true_errors=err, restarts=UNEVEN_R[d]))
@@ -353,9 +356,10 @@ def run_uneven(args):
     from paper_2509_17837_gb300 import autotune
     seed = 0xF1
     segs = uneven_segments(X, args.uneven_shots, seed)
-    # the tuner times short runs of a same-shaped batch of at most ~20k shots
-    tune_scale = min(1.0, 20000.0 / args.uneven_shots)
-    tune_segs = uneven_segments(X, args.uneven_shots, seed, scale_shots=tune_scale)
+    # the tuner times a batch of the same shots (at most 60k) with a tenth of
+    # the sweeps: the same chunks per distance, so the same waves and tails
+    tune_scale = min(1.0, 60000.0 / args.uneven_shots)
+    tune_segs = uneven_segments(X, args.uneven_shots, seed, scale_shots=tune_scale, scale_sweeps=0.1)
     class GraphForm:
         """A tuning candidate run the way the benchmark times it: modes 0, 3
         and 4 as captured graphs (one batch per mode, created on first use)."""
@@ -450,6 +454,7 @@ def run_uneven(args):
                             "persistent launch per distance class on forked streams; 0, 3 and 4 replayed as "
                             "captured CUDA graphs",
                    "autotune": {"batch_shots": int(sum(int(sg["syndromes"].shape[0]) for sg in tune_segs)),
+                                "sweeps": "a tenth of the workload's",
                                 "timings_s": timings},
                    "l2": "flushed between steps"},
         "move_attempts_per_s": att, "forms": {name: form_rec(name) for name in forms},

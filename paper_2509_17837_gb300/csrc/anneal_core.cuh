@@ -610,6 +610,22 @@ __device__ __forceinline__ void pair_phase(uint32_t (&P)[PairShape<D>::H][PairSh
   }
 }
 
+// Lists, in index order, the entries of a static (dE, class) table whose
+// threshold changes from sweep to sweep (class >= 0) as index << 16 | class;
+// run by one full warp.  Returns the count.
+__device__ __forceinline__ int list_threshold_entries(const int2* __restrict__ sig, int n, uint32_t* __restrict__ upd,
+                                                      int lane) {
+  int count = 0;
+  for (int base = 0; base < n; base += 32) {
+    const int idx = base + lane;
+    const int cls = idx < n ? sig[idx].y : -1;
+    const uint32_t m = __ballot_sync(0xFFFFFFFFu, cls >= 0);
+    if (cls >= 0) upd[count + __popc(m & ((1u << lane) - 1u))] = ((uint32_t)idx << 16) | (uint32_t)cls;
+    count += __popc(m);
+  }
+  return count;
+}
+
 __device__ __forceinline__ void sts_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
@@ -653,10 +669,11 @@ struct ChainOut {
 };
 
 // Shared memory of the row path: the static (dE, class) table, one per-sweep
-// table per warp, and the minimum-energy rows of every chain.
+// table per warp, the list of entries whose threshold changes per sweep, and
+// the minimum-energy rows of every chain.
 template <int D, int NT>
 __host__ __device__ constexpr size_t smem_rows() {
-  return kLutN * sizeof(int2) + (size_t)(NT / 32) * kLutN * sizeof(uint2) +
+  return kLutN * sizeof(int2) + (size_t)(NT / 32) * kLutN * sizeof(uint2) + kLutN * sizeof(uint32_t) + 16 +
          (size_t)D * NT * sizeof(typename Shape<D>::Row);
 }
 
@@ -684,8 +701,10 @@ __device__ __forceinline__ void anneal_cta_rows(const uint32_t* __restrict__ ini
                                                 uint8_t* smem) {
   using Row = typename Shape<D>::Row;
   int2* sig_static = reinterpret_cast<int2*>(smem);                                     // [kLutN]
-  uint2* lut_all = reinterpret_cast<uint2*>(smem + kLutN * sizeof(int2));               // [NT/32][kLutN]
-  Row* best_rows = reinterpret_cast<Row*>(smem + kLutN * sizeof(int2) + (NT / 32) * kLutN * sizeof(uint2));
+  uint2* lut_all = reinterpret_cast<uint2*>(sig_static + kLutN);                        // [NT/32][kLutN]
+  uint32_t* upd = reinterpret_cast<uint32_t*>(lut_all + (NT / 32) * kLutN);             // [kLutN]
+  int* n_upd_s = reinterpret_cast<int*>(upd + kLutN);                                   // [4]
+  Row* best_rows = reinterpret_cast<Row*>(n_upd_s + 4);
   const int tid = threadIdx.x, lane = tid & 31;
   uint2* L = lut_all + (tid >> 5) * kLutN;  // this warp's table
   SaDraws dr;
@@ -693,7 +712,13 @@ __device__ __forceinline__ void anneal_cta_rows(const uint32_t* __restrict__ ini
   const int n_sweeps = tab.n_sweeps;
 
   for (int idx = tid; idx < kLutN; idx += NT) sig_static[idx] = __ldg(&tab.sig[idx]);
-  __syncthreads();  // the only CTA barrier: warps then sweep independently
+  __syncthreads();
+  if (tid < 32) {  // the entries whose threshold changes from sweep to sweep
+    const int n = list_threshold_entries(sig_static, kLutN, upd, tid);
+    if (tid == 0) n_upd_s[0] = n;
+  }
+  __syncthreads();  // the last CTA barrier: warps then sweep independently
+  const int n_upd = n_upd_s[0];
   if (n_sweeps > 0) build_lut_warp(L, sig_static, tab.T, lane);
 
   Row R[D];
@@ -731,7 +756,11 @@ __device__ __forceinline__ void anneal_cta_rows(const uint32_t* __restrict__ ini
 #undef XZZX_PHASE
     if (t + 1 < n_sweeps) {  // next sweep's thresholds, once every lane is done with these
       __syncwarp();
-      build_lut_warp(L, sig_static, tab.T + (size_t)(t + 1) * tab.n_classes, lane);
+      const uint32_t* Trow = tab.T + (size_t)(t + 1) * tab.n_classes;
+      for (int k = lane; k < n_upd; k += 32) {  // only the thresholds of the dE > 0 entries change
+        const uint32_t v = upd[k];
+        L[v >> 16].y = __ldg(&Trow[v & 0xFFFFu]);
+      }
       __syncwarp();
     }
   }
@@ -768,15 +797,8 @@ __device__ __forceinline__ void anneal_cta_pairs(const uint32_t* __restrict__ in
 
   for (int idx = tid; idx < kPairLut; idx += NT) sig_pair[idx] = __ldg(&tab.sig[pair_sig_source(idx)]);
   __syncthreads();
-  if (tid < 32) {  // the entries whose threshold changes from sweep to sweep, in index order
-    int n = 0;
-    for (int base = 0; base < kPairLut; base += 32) {
-      const int idx = base + tid;
-      const int cls = idx < kPairLut ? sig_pair[idx].y : -1;
-      const uint32_t m = __ballot_sync(0xFFFFFFFFu, cls >= 0);
-      if (cls >= 0) upd[n + __popc(m & ((1u << tid) - 1u))] = ((uint32_t)idx << 16) | (uint32_t)cls;
-      n += __popc(m);
-    }
+  if (tid < 32) {  // the entries whose threshold changes from sweep to sweep
+    const int n = list_threshold_entries(sig_pair, kPairLut, upd, tid);
     if (tid == 0) n_upd_s[0] = n;
   }
   __syncthreads();  // the last CTA barrier: warps then sweep independently
