@@ -597,9 +597,10 @@ def run_large(args):
                          "attempts_per_s": S * 4 * R * N * (d * d - 1) / (e0.elapsed_time(e1) / 1e3)}
     mapping["identical_chain_minima"] = bool(torch.equal(best["thread_per_chain"], best["warp_per_chain"]))
 
-    # Occupancy sweep, one chain per thread: the same shots as one persistent
-    # launch with a given number of chains in flight per SM (CTAs per SM x
-    # chains per CTA).  Decisions must equal the plain decode of the same shots.
+    # Occupancy sweep: the same shots with a given number of chains in flight
+    # per SM (CTAs per SM x chains per CTA), one chain per thread as one
+    # persistent launch, then one chain per warp.  Decisions must equal the
+    # plain decode of the same shots.
     ref = X.decode_batch(code, noise, sched, sd, S, syn[S:2 * S], R, true_errors=err[S:2 * S], stream=stream)
     occupancy = []
     if not args.no_occupancy_sweep:
@@ -617,7 +618,28 @@ def run_large(args):
             same = all(torch.equal(o[k], ref[k]) for k in ("cls", "E4", "recovery", "fail"))
             info = b.info()
             in_flight = info["persistent_grid"] * nt // props.multi_processor_count
-            occupancy.append({"chains_per_cta": nt, "ctas_per_sm": cps, "chains_in_flight_per_sm": in_flight,
+            occupancy.append({"mapping": "thread_per_chain", "chains_per_cta": nt, "ctas_per_sm": cps,
+                              "chains_in_flight_per_sm": in_flight,
+                              "ms": e0.elapsed_time(e1),
+                              "attempts_per_s": info["move_attempts"] / (e0.elapsed_time(e1) / 1e3),
+                              "identical_decisions": bool(same)})
+            b.close()
+        # One warp per chain (mode 2, 4 chains per CTA): resident CTAs per SM
+        # capped by padding each CTA's shared memory (0 = the register limit).
+        for cps in (2, 4, 8, 0):
+            seg = dict(code=code, noise=noise, sched=sched, shot0=S, syndromes=syn[S:2 * S], restarts=R,
+                       true_errors=err[S:2 * S])
+            b = X.Batch([seg], sd, ctas_per_sm=cps)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(2, stream)
+            e1.record(stream)
+            e1.synchronize()
+            o = b.outputs[0]
+            same = all(torch.equal(o[k], ref[k]) for k in ("cls", "E4", "recovery", "fail"))
+            info = b.info()
+            occupancy.append({"mapping": "warp_per_chain", "chains_per_cta": 4, "ctas_per_sm_cap": cps,
+                              "chains_in_flight_per_sm": 4 * info["warp_ctas_per_sm"],
                               "ms": e0.elapsed_time(e1),
                               "attempts_per_s": info["move_attempts"] / (e0.elapsed_time(e1) / 1e3),
                               "identical_decisions": bool(same)})

@@ -298,7 +298,8 @@ typedef struct {
 } xzzx_segment;
 
 typedef struct {
-  int32_t ctas_per_sm;    /* persistent grid = SMs x this; 0 = the occupancy maximum */
+  int32_t ctas_per_sm;    /* persistent grid = SMs x this; 0 = the occupancy maximum.  Mode 2: resident
+                             CTAs (4 chains each) per SM capped at this by padding each CTA's shared memory */
   int32_t order;          /* chunk queue: 0 = longest chunks first, 1 = segment order */
   int32_t graph_mode;     /* the mode xzzx_batch_run_graph captures: 0, 3 or 4 */
   int32_t chains_per_cta; /* chains per CTA of the annealing launches (chunk size): 128 or 256; 0 = 128 */
@@ -313,6 +314,7 @@ typedef struct {
   int64_t total_shots;
   int32_t chains_per_cta, sweep_unroll;
   int32_t n_classes;     /* distance classes present (d <= 15, 17..21, 23..31): mode 4's launches */
+  int32_t warp_ctas_per_sm; /* mode 2: resident CTAs (4 chains each) per SM, fewest over the distances */
 } xzzx_batch_info;
 
 typedef struct xzzx_batch xzzx_batch;

@@ -48,7 +48,8 @@ class BatchInfo(C.Structure):
     _fields_ = [("n_segments", C.c_int32), ("n_chunks", C.c_int32), ("n_distances", C.c_int32),
                 ("persistent_grid", C.c_int32), ("launches_batched", C.c_int32), ("launches_plain", C.c_int32),
                 ("workspace_bytes", C.c_size_t), ("move_attempts", C.c_double), ("total_shots", C.c_int64),
-                ("chains_per_cta", C.c_int32), ("sweep_unroll", C.c_int32), ("n_classes", C.c_int32)]
+                ("chains_per_cta", C.c_int32), ("sweep_unroll", C.c_int32), ("n_classes", C.c_int32),
+                ("warp_ctas_per_sm", C.c_int32)]
 
 
 class ServeCfg(C.Structure):

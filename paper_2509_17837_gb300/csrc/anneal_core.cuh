@@ -23,7 +23,9 @@
 // Sweep.  Colours 0..3 in order (faces of one colour have disjoint supports,
 // so their order inside a colour does not matter).  Inside a colour the loop
 // runs over the face columns at run time and unrolls the rows, so register
-// indices stay compile-time constants and the code stays small at any d.
+// indices stay compile-time constants and the code stays small at any d (pair
+// path: one loop per 32-bit register with the register-edge columns peeled
+// for d <= 11, one loop over 64-bit pair words for d = 13, 15).
 //
 // Acceptance.  The corner signature indexes a per-sweep table of (dE, A): A =
 // T[t][dE] for dE > 0 and A = 0 otherwise, so a move is accepted iff dE <= 0
@@ -557,13 +559,91 @@ __device__ __forceinline__ void pair_register_columns(uint32_t (&P)[PairShape<D>
   }
 }
 
+// Bits [sh, sh + 32) of a pair word (zeros above it), sh < 64.
+template <int NW>
+__device__ __forceinline__ uint32_t pair_bits(const uint32_t (&w)[NW], uint32_t sh) {
+  if constexpr (NW == 1) return w[0] >> sh;
+  else return (uint32_t)((((uint64_t)w[1] << 32) | w[0]) >> sh);
+}
+
+// One column of faces of colour C at column b >= 1 of the pair words (two
+// registers at most), the column a run-time value.
+template <int D, int C>
+__device__ __forceinline__ void pair_column_rt(uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW], int32_t& E,
+                                               uint32_t Lb, const SaDraws& dr, const PhiloxKeys& K, int b,
+                                               uint32_t* err) {
+  constexpr int H = PairShape<D>::H, NW = PairShape<D>::NW;
+  static_assert(NW <= 2, "pair words of at most two registers");
+  constexpr int NR = (C == 0 || C == 3) ? H : H - 1;
+  constexpr int JOFF = (C == 1) ? 1 : 0;
+  constexpr int IAOFF = (C == 1) ? 1 : 0;
+  constexpr int NG = (NR - 1 + IAOFF) / 4 + 1;
+  const uint32_t ib = (uint32_t)(b + 1) >> 1;
+  const uint32_t s = 4u * (uint32_t)b;
+  uint2 e[NR];
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    uint32_t a;
+    if (C == 3 && j == 0)
+      a = (pair_bits<NW>(P[0], s - 1u) & 0x198u) | (Lb + kPairTop * 8);
+    else if (C == 0 && j == NR - 1)
+      a = (pair_bits<NW>(P[j], s - 3u) & 0x198u) | (Lb + kPairBottom * 8);
+    else
+      a = (pair_bits<NW>(P[j + JOFF], s - 3u) & 0x7F8u) | Lb;
+    e[j] = pair_entry(a, Lb, err);
+  }
+  uint4 r[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    uint32_t need = 0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j)
+      if (((j + IAOFF) >> 2) == g) need |= e[j].y;
+    r[g] = make_uint4(0u, 0u, 0u, 0u);
+    if (__any_sync(0xFFFFFFFFu, need != 0u)) r[g] = dr.block(((uint32_t)C << 16) | (ib << 8) | (uint32_t)g, K);
+  }
+  using M = typename std::conditional<NW == 1, uint32_t, uint64_t>::type;
+  const M m_bulk = (M)0x96u << s, m_top = (M)0x84u << s, m_bottom = (M)0x12u << s;
+#pragma unroll
+  for (int j = 0; j < NR; ++j) {
+    const int ia = j + IAOFF;
+    const uint32_t u = lane_of(r[ia >> 2], ia & 3);
+    const int32_t dE = (int32_t)e[j].x;
+    if ((dE <= 0) | (u < e[j].y)) {
+      E += dE;
+      const int row = (C == 3 && j == 0) ? 0 : (C == 0 && j == NR - 1) ? j : j + JOFF;
+      const M m = (C == 3 && j == 0) ? m_top : (C == 0 && j == NR - 1) ? m_bottom : m_bulk;
+      P[row][0] ^= (uint32_t)m;
+      if constexpr (NW == 2) P[row][1] ^= (uint32_t)((uint64_t)m >> 32);
+    }
+  }
+}
+
+// The bulk columns of colour C for d >= 13: b = 0 (even-b colours) with its
+// bits at the bottom of register 0, then every other column in one run-time
+// loop over 64-bit pair words.  Against the per-register form this costs
+// about one instruction per column for the shifted masks but cuts the sweep
+// body several-fold, which pays once the body outgrows instruction fetch
+// (d = 13, 15); at d <= 11 the per-register form is faster.
+template <int D, int C>
+__device__ __forceinline__ void pair_bulk_columns(uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW], int32_t& E,
+                                                  uint32_t Lb, const SaDraws& dr, const PhiloxKeys& K,
+                                                  uint32_t* err) {
+  constexpr int PB = C >> 1;
+  constexpr int BMAX = PB + 2 * ((D - 1) / 2 - 1);  // the colour's last bulk column
+  if constexpr (PB == 0) pair_column<D, C, kAt0>(P, E, Lb, dr, K, 0, 0u, err);
+#pragma unroll 1
+  for (int b = PB == 0 ? 2 : 1; b <= BMAX; b += 2) pair_column_rt<D, C>(P, E, Lb, dr, K, b, err);
+}
+
 // One colour phase of one sweep (pair layout: even for colours 0 and 2, odd
 // for 1 and 3).
 template <int D, int C>
 __device__ __forceinline__ void pair_phase(uint32_t (&P)[PairShape<D>::H][PairShape<D>::NW], int32_t& E, uint32_t Lb,
                                            const SaDraws& dr, const PhiloxKeys& K, uint32_t* err) {
   constexpr int H = PairShape<D>::H;
-  pair_register_columns<D, C, 0>(P, E, Lb, dr, K, err);
+  if constexpr (D >= 13) pair_bulk_columns<D, C>(P, E, Lb, dr, K, err);
+  else pair_register_columns<D, C, 0>(P, E, Lb, dr, K, err);
   if constexpr (C == 1 || C == 2) {
     // Boundary column: right (b = d-1: TL and BL) for colour 1, left (b = -1:
     // TR and BR) for colour 2, over the bulk rows of the colour.

@@ -105,6 +105,8 @@ extern "C" xzzx_status xzzx_anneal_warp(const xzzx_code* code, const xzzx_schedu
 // ---------------------------------------------------------------------------
 #include "batch_internal.h"
 
+#include <algorithm>
+
 namespace xzzx {
 namespace batch {
 namespace {
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(kWPC * 32) warp_chains_kernel(const __grid_con
 
 template <int D>
 xzzx_status warp_chains_d(const WarpLaunch& L, cudaStream_t stream) {
-  constexpr size_t smem = warpchain::smem_bytes<D, kWPC>();
+  const size_t smem = std::max(warpchain::smem_bytes<D, kWPC>(), (size_t)std::max(L.smem, 0));
   if (L.n_chains <= 0) return XZZX_OK;
   const int64_t grid = (L.n_chains + kWPC - 1) / kWPC;
   if (grid > 0x7FFFFFFF) return fail(XZZX_EINVAL, "too many chains for one launch");
@@ -159,7 +161,44 @@ xzzx_status warp_chains_d(const WarpLaunch& L, cudaStream_t stream) {
   return XZZX_OK;
 }
 
+// Shared memory per CTA that holds the kernel at no more than cap resident
+// CTAs per SM (cap 0: its own need, no cap); the kernel is set to prefer the
+// largest shared-memory carveout so the cap is what decides.
+template <int D>
+xzzx_status warp_chains_configure_d(int cap, int* smem_out, int* ctas_per_sm) {
+  size_t smem = warpchain::smem_bytes<D, kWPC>();
+  int dev = 0, per_sm_bytes = 0, reserved = 0, optin = 0;
+  XZZX_CUDA_TRY(cudaGetDevice(&dev));
+  XZZX_CUDA_TRY(cudaDeviceGetAttribute(&per_sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+  XZZX_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  XZZX_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (cap > 0) {
+    const long pad = ((long)per_sm_bytes / cap - reserved) & ~15L;
+    smem = std::max(smem, (size_t)std::min<long>(pad, optin));
+  }
+  XZZX_CUDA_TRY(cudaFuncSetAttribute(warp_chains_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  XZZX_CUDA_TRY(cudaFuncSetAttribute(warp_chains_kernel<D>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     (int)cudaSharedmemCarveoutMaxShared));
+  XZZX_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, warp_chains_kernel<D>, kWPC * 32, smem));
+  *smem_out = (int)smem;
+  return XZZX_OK;
+}
+
 }  // namespace
+
+xzzx_status configure_warp_chains(int d, int cap, int* smem, int* ctas_per_sm) {
+  switch (d) {
+#define XZZX_CASE(DD) \
+  case DD:            \
+    return warp_chains_configure_d<DD>(cap, smem, ctas_per_sm);
+    XZZX_CASE(3) XZZX_CASE(5) XZZX_CASE(7) XZZX_CASE(9) XZZX_CASE(11) XZZX_CASE(13) XZZX_CASE(15)
+    XZZX_CASE(17) XZZX_CASE(19) XZZX_CASE(21) XZZX_CASE(23) XZZX_CASE(25) XZZX_CASE(27) XZZX_CASE(29)
+    XZZX_CASE(31)
+#undef XZZX_CASE
+    default:
+      return fail(XZZX_EUNSUPPORTED, "no annealing kernel for this distance");
+  }
+}
 
 xzzx_status launch_warp_chains(int d, const WarpLaunch& L, cudaStream_t stream) {
   switch (d) {

@@ -401,6 +401,7 @@ xzzx_status launch_plan(const Plan& p, const PlanDev& d, const PhiloxKeys& K, in
       W.n_segs = (int)p.segs.size();
       W.chain0 = p.chain_prefix[r.seg_begin];
       W.n_chains = p.chain_prefix[r.seg_end] - p.chain_prefix[r.seg_begin];
+      W.smem = r.warp_smem;
       if ((st = launch_warp_chains(r.d, W, stream))) return st;
     } else if ((st = launch_chunks(r.d, p.nt, p.unroll,
                                    anneal_launch(d, K, d.byd, r.chunk_begin, r.chunk_end - r.chunk_begin, nullptr), stream))) {
@@ -427,6 +428,7 @@ struct xzzx_batch {
   cudaGraphExec_t graph_exec = nullptr;
   int graph_mode = 0;
   int class_grid[xzzx::batch::kNumClasses] = {0, 0, 0};  // mode 4: persistent grid of each class
+  int warp_per_sm = 0;  // mode 2: resident warp-kernel CTAs per SM (fewest over the distances)
   // modes 3 and 4: one side stream and one completion event per distance (or
   // class), and the fork event, created on first use
   std::vector<cudaStream_t> side;
@@ -582,6 +584,15 @@ xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t see
     if (cfg && cfg->ctas_per_sm > 0) cls_per_sm = std::min(cls_per_sm, cfg->ctas_per_sm);
     b->class_grid[r.cls] = n_sm * cls_per_sm;
   }
+  b->warp_per_sm = 0;
+  for (DistanceRange& r : b->plan.ranges) {
+    int w_per_sm = 0;
+    if ((st = configure_warp_chains(r.d, cfg ? cfg->ctas_per_sm : 0, &r.warp_smem, &w_per_sm))) {
+      free_batch(b);
+      return st;
+    }
+    b->warp_per_sm = b->warp_per_sm ? std::min(b->warp_per_sm, w_per_sm) : w_per_sm;
+  }
   b->graph_mode = cfg ? cfg->graph_mode : 0;
   if (b->graph_mode != 0 && b->graph_mode != 3 && b->graph_mode != 4) {
     free_batch(b);
@@ -645,6 +656,7 @@ xzzx_status xzzx_batch_get_info(const xzzx_batch* b, xzzx_batch_info* out) {
   out->total_shots = b->plan.total_shots;
   out->chains_per_cta = b->plan.nt;
   out->sweep_unroll = b->plan.unroll;
+  out->warp_ctas_per_sm = b->warp_per_sm;
   return XZZX_OK;
 }
 

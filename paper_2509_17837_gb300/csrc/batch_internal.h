@@ -54,6 +54,7 @@ struct DistanceRange {
   int d;
   int seg_begin, seg_end;        // segments [begin, end) (ordered by distance)
   int chunk_begin, chunk_end;    // chunks_byd range
+  int warp_smem = 0;             // mode 2: shared memory per CTA of the warp kernel (0: its own need)
 };
 
 // Distance classes of the persistent kernels: d <= 15, 17..21, 23..31.
@@ -143,8 +144,13 @@ struct WarpLaunch {
   const int64_t* chain_prefix;
   int n_segs;
   int64_t chain0, n_chains;
+  int smem;  // dynamic shared memory per CTA; below the kernel's need means its need
 };
 xzzx_status launch_warp_chains(int d, const WarpLaunch& L, cudaStream_t stream);
+// Configure the distance-d warp kernel for at most cap resident CTAs per SM
+// (0: no cap) by padding its shared memory: bytes per CTA to *smem, the
+// resulting resident CTAs per SM to *ctas_per_sm.
+xzzx_status configure_warp_chains(int d, int cap, int* smem, int* ctas_per_sm);
 
 }  // namespace batch
 }  // namespace xzzx

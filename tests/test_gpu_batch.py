@@ -164,3 +164,23 @@ def test_batch_tuning_variants_identical(env, nt, unroll):
         assert_same(b.outputs, refs)
     with pytest.raises(X.XzzxError):
         X.Batch(segs, seed, chains_per_cta=64)
+
+
+@pytest.mark.parametrize("cap", [1, 2, 4])
+def test_batch_warp_mapping_occupancy_cap(env, cap):
+    """Mode 2 (one warp per chain) with its resident CTAs per SM capped by
+    padded shared memory: at most cap CTAs per SM, and outputs identical to
+    the per-segment calls."""
+    X, torch = env
+    seed = 0x3A9C
+    segs = make_segments(X, torch, seed)
+    refs = reference_outputs(X, torch, segs, seed)
+    free = X.Batch(segs, seed)
+    b = X.Batch(segs, seed, ctas_per_sm=cap)
+    assert 1 <= b.info()["warp_ctas_per_sm"] <= cap
+    assert free.info()["warp_ctas_per_sm"] >= b.info()["warp_ctas_per_sm"]
+    b.run(2)
+    torch.cuda.synchronize()
+    assert_same(b.outputs, refs)
+    free.close()
+    b.close()
