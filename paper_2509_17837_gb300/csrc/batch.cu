@@ -112,17 +112,20 @@ struct GreedyLaunch {
   int64_t cta0;
 };
 
-__global__ void __launch_bounds__(kGreedyWarps * 32) greedy_batch_kernel(const __grid_constant__ GreedyLaunch G) {
-  __shared__ greedy::Shared S;
+template <bool L>
+__global__ void __launch_bounds__(kGreedyWarps * 32, L ? greedy::RotGeo::kMinCtasLists : 1)
+    greedy_batch_kernel(const __grid_constant__ GreedyLaunch G) {
+  __shared__ greedy::SharedT<greedy::RotGeo, L> S;
   const int64_t b = G.cta0 + blockIdx.x;
   const int s = find_segment(G.cta_prefix, G.n_segs, b);
   const SegDev& sg = G.segs[s];
   const int64_t local = b - G.cta_prefix[s];
   const int64_t k = local / sg.greedy_groups;
   const int group = (int)(local % sg.greedy_groups);
-  greedy::greedy_cta(sg.code, G.keys, sg.shot0 + (uint64_t)k, group, sg.restarts, sg.randomised, sg.Wt_x, sg.Wt_z,
-                     sg.syndromes + (size_t)k * sg.code.sw, sg.init + (size_t)k * sg.restarts * 2 * sg.code.w,
-                     sg.cbits + (size_t)k * sg.restarts, S);
+  greedy::greedy_cta<greedy::RotGeo, L>(sg.code, G.keys, sg.shot0 + (uint64_t)k, group, sg.restarts, sg.greedy_rpw,
+                                        sg.randomised, sg.Wt_x, sg.Wt_z, sg.syndromes + (size_t)k * sg.code.sw,
+                                        sg.init + (size_t)k * sg.restarts * 2 * sg.code.w,
+                                        sg.cbits + (size_t)k * sg.restarts, S);
 }
 
 struct ReduceLaunch {
@@ -157,8 +160,17 @@ xzzx_status run_greedy(const Plan& p, const PlanDev& d, const PhiloxKeys& K, int
   G.segs = d.segs;
   G.cta_prefix = d.cta_prefix;
   G.n_segs = (int)p.segs.size();
-  G.cta0 = cta0;
-  greedy_batch_kernel<<<(unsigned)n_ctas, kGreedyWarps * 32, 0, stream>>>(G);
+  // Segments are ordered by distance: CTAs before list_cta_end (d <= 15) run
+  // the kernel with candidate lists, the rest the one without.
+  const int64_t end = cta0 + n_ctas, split = std::min(std::max(p.list_cta_end, cta0), end);
+  if (split > cta0) {
+    G.cta0 = cta0;
+    greedy_batch_kernel<true><<<(unsigned)(split - cta0), kGreedyWarps * 32, 0, stream>>>(G);
+  }
+  if (end > split) {
+    G.cta0 = split;
+    greedy_batch_kernel<false><<<(unsigned)(end - split), kGreedyWarps * 32, 0, stream>>>(G);
+  }
   XZZX_CUDA_TRY(cudaGetLastError());
   return XZZX_OK;
 }
@@ -230,6 +242,16 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
   P.chain_prefix.assign(n_segs + 1, 0);
   size_t ws = 0;
   std::vector<ChunkDev> chunks;
+  // Restarts per greedy warp: the largest count that leaves the whole greedy
+  // launch enough CTAs.
+  int rpw = 1;
+  for (int r = greedy::kMaxRestartsPerWarp; r > 1 && rpw == 1; r >>= 1) {
+    int64_t ctas = 0;
+    for (int j = 0; j < n_segs; ++j)
+      ctas += (int64_t)segs[j].n_shots *
+              greedy::greedy_groups(segs[j].restarts, segs[j].code->d <= greedy::kListMaxD ? r : 1);
+    if (ctas >= greedy::kMinGreedyCtas) rpw = r;
+  }
   for (int j = 0; j < n_segs; ++j) {
     const xzzx_segment& s = segs[order[j]];
     const size_t n = (size_t)s.n_shots, R = (size_t)s.restarts, w = (size_t)s.code->w;
@@ -239,7 +261,8 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
     d.n_shots = s.n_shots;
     d.restarts = s.restarts;
     d.randomised = s.randomised;
-    d.greedy_groups = (s.restarts + kGreedyWarps - 1) / kGreedyWarps;
+    d.greedy_rpw = s.code->d <= greedy::kListMaxD ? rpw : 1;  // several per warp only with candidate lists
+    d.greedy_groups = greedy::greedy_groups(s.restarts, d.greedy_rpw);
     d.Wt_x = s.noise->Wt_x;
     d.Wt_z = s.noise->Wt_z;
     d.syndromes = s.syndromes;
@@ -260,6 +283,7 @@ xzzx_status build_plan(const xzzx_segment* segs, int n_segs, int device, int ord
     d.n_classes = s.sched->n_classes;
     for (int k = 0; k < 4; ++k) d.W[k] = s.sched->noise.W[k];
     P.cta_prefix[j + 1] = P.cta_prefix[j] + (int64_t)s.n_shots * d.greedy_groups;
+    if (s.code->d <= greedy::kListMaxD) P.list_cta_end = P.cta_prefix[j + 1];
     P.shot_prefix[j + 1] = P.shot_prefix[j] + s.n_shots;
     P.chain_prefix[j + 1] = P.chain_prefix[j] + (int64_t)s.n_shots * s.restarts * 4;
     P.dmax = std::max(P.dmax, s.code->d);

@@ -14,7 +14,7 @@ constexpr int kNT = 128;  // default chains per CTA of the batched anneal launch
 struct SegDev {
   DevCode code;
   uint64_t shot0;
-  int n_shots, restarts, randomised, greedy_groups;
+  int n_shots, restarts, randomised, greedy_groups, greedy_rpw;
   int32_t Wt_x, Wt_z;
   const uint32_t* syndromes;
   const uint32_t* true_errors;
@@ -81,6 +81,7 @@ struct Plan {
   int dmax = 0;
   double attempts = 0;
   int64_t total_shots = 0, total_ctas = 0;
+  int64_t list_cta_end = 0;  // greedy CTAs [0, list_cta_end) are of segments with d <= 15
   size_t workspace_bytes = 0;
 };
 

@@ -11,20 +11,21 @@ struct GreedyArgs {
   DevCode code;
   PhiloxKeys keys;
   uint64_t shot0;
-  int n_shots, restarts, randomised, groups;
+  int n_shots, restarts, randomised, groups, rpw;
   int32_t Wt_x, Wt_z;
   const uint32_t* syndromes;
   uint32_t* init;
   uint8_t* cbits;
 };
 
-template <class G>
-__global__ void __launch_bounds__(kWarps * 32) greedy_kernel(const __grid_constant__ GreedyArgs A) {
-  __shared__ SharedT<G> S;
+template <class G, bool L>
+__global__ void __launch_bounds__(kWarps * 32, L ? G::kMinCtasLists : 1)
+    greedy_kernel(const __grid_constant__ GreedyArgs A) {
+  __shared__ SharedT<G, L> S;
   const int k = blockIdx.x / A.groups;
-  greedy_cta<G>(A.code, A.keys, A.shot0 + (uint64_t)k, blockIdx.x % A.groups, A.restarts, A.randomised, A.Wt_x,
-                A.Wt_z, A.syndromes + (size_t)k * A.code.sw, A.init + (size_t)k * A.restarts * 2 * A.code.w,
-                A.cbits + (size_t)k * A.restarts, S);
+  greedy_cta<G, L>(A.code, A.keys, A.shot0 + (uint64_t)k, blockIdx.x % A.groups, A.restarts, A.rpw, A.randomised,
+                   A.Wt_x, A.Wt_z, A.syndromes + (size_t)k * A.code.sw,
+                   A.init + (size_t)k * A.restarts * 2 * A.code.w, A.cbits + (size_t)k * A.restarts, S);
 }
 
 }  // namespace
@@ -40,7 +41,13 @@ xzzx_status launch_greedy(const xzzx_code* code, const xzzx_noise* noise, uint64
   A.n_shots = n_shots;
   A.restarts = restarts;
   A.randomised = randomised;
-  A.groups = (restarts + kWarps - 1) / kWarps;
+  A.rpw = 1;  // several restarts per warp only with candidate lists (d <= 15)
+  for (int r = kMaxRestartsPerWarp; r > 1 && code->layout != kLayoutPlanar && code->d <= kListMaxD; r >>= 1)
+    if ((int64_t)n_shots * greedy_groups(restarts, r) >= kMinGreedyCtas) {
+      A.rpw = r;
+      break;
+    }
+  A.groups = greedy_groups(restarts, A.rpw);
   A.Wt_x = noise->Wt_x;
   A.Wt_z = noise->Wt_z;
   A.syndromes = syndromes;
@@ -49,9 +56,11 @@ xzzx_status launch_greedy(const xzzx_code* code, const xzzx_noise* noise, uint64
   const uint64_t grid = (uint64_t)n_shots * A.groups;
   if (grid > 0x7FFFFFFFull) return fail(XZZX_EINVAL, "too many shots x restarts for one launch");
   if (code->layout == kLayoutPlanar)
-    greedy_kernel<PlanarGeo><<<(unsigned)grid, kWarps * 32, 0, stream>>>(A);
+    greedy_kernel<PlanarGeo, false><<<(unsigned)grid, kWarps * 32, 0, stream>>>(A);
+  else if (code->d <= kListMaxD)
+    greedy_kernel<RotGeo, true><<<(unsigned)grid, kWarps * 32, 0, stream>>>(A);
   else
-    greedy_kernel<RotGeo><<<(unsigned)grid, kWarps * 32, 0, stream>>>(A);
+    greedy_kernel<RotGeo, false><<<(unsigned)grid, kWarps * 32, 0, stream>>>(A);
   XZZX_CUDA_TRY(cudaGetLastError());
   return XZZX_OK;
 }

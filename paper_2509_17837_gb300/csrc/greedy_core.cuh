@@ -1,9 +1,13 @@
 // Randomised greedy matching (Algs. 5 and 6) on the GPU.
 //
-// One CTA per (shot, group of kWarps restarts); one warp per restart.  The CTA
-// first computes, in shared memory, each face's shortest distance to the open
-// boundary of its decoding graph (w(u,b) of Eq. distance_u_boundary) by
-// Bellman-Ford relaxation, and the defect list of each decoding-graph colour.
+// One CTA per (shot, group of kWarps*rpw restarts); each warp takes rpw
+// restarts in turn (for d <= 15 rpw = 4, 2 or 1, the most that still leaves
+// the launch several waves of CTAs; 1 above).  The CTA first computes, in
+// shared memory, each face's shortest distance to the open boundary of its
+// decoding graph (w(u,b) of Eq. distance_u_boundary) by Bellman-Ford
+// relaxation, and the defect list of each decoding-graph colour; for d <= 15,
+// also every vertex's candidate list (below).  All of it depends on the shot
+// only, so it serves every restart of the CTA.
 //
 // Matching.  All candidate pairs are totally ordered by (w, key, u, v): w the
 // pair weight of Eq. distance_u_v_def_new, key a Philox draw per pair (Alg. 6)
@@ -11,7 +15,12 @@
 // vertex).  Scanning that order and keeping pairs whose ends are free gives
 // the same matching as repeatedly matching every pair that is the best
 // remaining pair of both its ends ("locally dominant" pairs), which is what
-// the warp does, round by round, in parallel over vertices.
+// the warp does, round by round, in parallel over vertices.  A vertex's best
+// free partner is found from its candidate list when the colour has at most
+// 64 vertices: the other vertices sorted by (w, index), so the first free
+// entry has the lowest weight and, among equal weights, the lowest (u, v);
+// with random keys only the free entries tied with it at that weight are
+// compared further.  Larger colours scan all candidates.
 //
 // Paths.  Every kept pair is joined by a canonical shortest path (a Z step
 // toward the target whenever one is needed and possible, else an X step; to
@@ -22,6 +31,8 @@
 // error area.
 #pragma once
 
+#include <type_traits>
+
 #include "internal.h"
 #include "philox.cuh"
 
@@ -29,6 +40,18 @@ namespace xzzx {
 namespace greedy {
 
 constexpr int kWarps = 4;
+// A launch with candidate lists takes the largest restarts-per-warp count (4,
+// 2 or 1) that still gives it this many CTAs (several waves on a 152-SM GPU):
+// large launches then share each CTA's setup across more restarts, small ones
+// keep their CTAs.  Without lists (d > 15) a warp takes one restart: the scan
+// dominates there, and longer CTAs only lengthen the launch's tail.
+constexpr int64_t kMinGreedyCtas = 4096;
+constexpr int kMaxRestartsPerWarp = 4;
+
+// CTAs of a shot's restarts at rpw restarts per warp.
+__host__ __device__ inline int greedy_groups(int restarts, int rpw) {
+  return (restarts + kWarps * rpw - 1) / (kWarps * rpw);
+}
 // Reference modes: greedy matching with lexicographic ties (Alg. 5), with
 // random ties (Alg. 6), or every defect joined to its nearer boundary.
 constexpr int kInitGreedy = 0, kInitGreedyRandom = 1, kInitBoundary = 2;
@@ -38,6 +61,10 @@ constexpr int32_t kInf = 0x3FFFFFFF;
 // (r, c) = r*d + c.  The four edges of a face in walking order: Z(+1,+1),
 // Z(-1,-1), X(+1,-1), X(-1,+1), crossing the qubit (max a, max b).
 struct RotGeo {
+  static constexpr bool kSortedLists = true;
+  // Resident CTAs per SM the kernel with candidate lists is register-bounded
+  // for (64 registers; its shared memory allows 7).
+  static constexpr int kMinCtasLists = 8;
   static constexpr int kMaxFaces = kMaxD * kMaxD - 1;
   static constexpr int kMaxAt = (kMaxD + 1) * (kMaxD + 1);
   static constexpr int kMaxWords = (kMaxD * kMaxD + 31) / 32;
@@ -63,6 +90,8 @@ struct RotGeo {
 // grid; qubits on the sites with r + c even.  Edges in walking order: Z right
 // and Z left (crossing (i, j+-1)), X down and X up (crossing (i+-1, j)).
 struct PlanarGeo {
+  static constexpr bool kSortedLists = false;
+  static constexpr int kMinCtasLists = 1;
   static constexpr int kMaxFaces = 2 * kMaxD * (kMaxD - 1);
   static constexpr int kMaxAt = (2 * kMaxD - 1) * (2 * kMaxD - 1);
   static constexpr int kMaxWords = (kMaxD * kMaxD + (kMaxD - 1) * (kMaxD - 1) + 31) / 32;
@@ -91,8 +120,25 @@ struct PlanarGeo {
   }
 };
 
+// Sorted candidate lists of one CTA (rotated codes): for each colour with at
+// most kListMax vertices and each vertex x, the other vertices y in
+// increasing (w(x, y), y), one byte each: y, plus 0x80 when w(x, y) equals the
+// previous entry's weight.  cur: each warp's first possibly-free entry.
+constexpr int kListMax = 64;
+struct CandidateLists {
+  uint8_t l[2][kListMax][kListMax];
+  uint8_t cur[kWarps][kListMax];
+  int usable[2];
+};
+struct NoLists {};
+
+// Largest distance whose greedy launches carry candidate lists.  Past it most
+// colours hold more than kListMax vertices at the noise of interest, and the
+// lists' shared memory would only lower the occupancy of the scan that runs.
+constexpr int kListMaxD = 15;
+
 template <class G>
-struct SharedT {
+struct SharedBase {
   int16_t fa[G::kMaxFaces], fb[G::kMaxFaces];
   int16_t at[G::kMaxAt];
   int32_t wb[G::kMaxFaces];
@@ -104,11 +150,17 @@ struct SharedT {
   uint32_t cfg[kWarps][2 * G::kMaxWords];
   int walk_error[kWarps];
 };
-using Shared = SharedT<RotGeo>;
+
+// A CTA's shared state, with candidate lists when L (rotated codes only).
+template <class G, bool L>
+struct SharedT : SharedBase<G> {
+  static constexpr bool kLists = G::kSortedLists && L;
+  typename std::conditional<kLists, CandidateLists, NoLists>::type lists;
+};
 
 template <class G>
 struct Ctx {
-  const SharedT<G>& S;
+  const SharedBase<G>& S;
   int d, w;
   int32_t Wt_x, Wt_z;
   uint32_t* err;  // the code's device error area
@@ -187,82 +239,82 @@ __device__ bool walk_boundary(const Ctx<G>& X, int u, uint32_t* cfg) {
   return false;
 }
 
-// One CTA: references of restarts [group*kWarps, group*kWarps + kWarps)
-// of one shot.  syn: the shot's syndrome words; init / cbits: the shot's rows
-// (restarts x 2w words, restarts bytes).
+// Pair weight of vertices x != y of a colour with nd defects (vertex nd is the
+// virtual boundary vertex).
 template <class G>
-__device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K, uint64_t shot, int group, int restarts,
-                                           int mode, int32_t Wt_x, int32_t Wt_z, const uint32_t* __restrict__ syn,
-                                           uint32_t* __restrict__ init, uint8_t* __restrict__ cbits, SharedT<G>& S) {
-  const int d = C.d, ns = C.ns, w = C.w;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int i = group * kWarps + warp;
+__device__ __forceinline__ int32_t pair_weight(const Ctx<G>& X, const int16_t* D, int nd, int x, int y) {
+  if (x == nd) return X.S.wb[D[y]];
+  if (y == nd) return X.S.wb[D[x]];
+  return min(X.w_int(D[x], D[y]), X.S.wb[D[x]] + X.S.wb[D[y]]);
+}
 
-  for (int f = tid; f < ns; f += blockDim.x) {
-    S.fa[f] = C.face_a[f];
-    S.fb[f] = C.face_b[f];
-  }
-  for (int j = tid; j < G::at_size(d); j += blockDim.x) S.at[j] = C.face_at[j];
-  for (int j = tid; j < C.sw; j += blockDim.x) S.syn[j] = syn[j];
-  __syncthreads();
-  Ctx<G> X{S, d, w, Wt_x, Wt_z, C.err, C.nq};
+// Keep the smaller (keep_min) or larger of v and the value of lane ^ j.
+__device__ __forceinline__ uint32_t bitonic_step(uint32_t v, int j, bool keep_min) {
+  const uint32_t o = __shfl_xor_sync(0xFFFFFFFFu, v, j);
+  return keep_min ? min(v, o) : max(v, o);
+}
 
-  // Boundary distances: start from the boundary edges, relax until stable.
-  for (int f = tid; f < ns; f += blockDim.x) {
-    const int a = S.fa[f], b = S.fb[f];
-    int32_t best = kInf;
-    for (int e = 0; e < 4; ++e) {
-      int na, nb, qr, qc;
-      G::step(a, b, e, na, nb, qr, qc);
-      if (X.qubit(qr, qc) < 0 || X.face(na, nb) >= 0) continue;
-      best = min(best, e < 2 ? Wt_z : Wt_x);
-    }
-    S.wb[f] = best;
-  }
-  __syncthreads();
-  for (int iter = 0; iter < ns + 1; ++iter) {
-    int changed = 0;
-    for (int f = tid; f < ns; f += blockDim.x) {
-      const int a = S.fa[f], b = S.fb[f];
-      int32_t cur = S.wb[f];
-      for (int e = 0; e < 4; ++e) {
-        int na, nb, qr, qc;
-        G::step(a, b, e, na, nb, qr, qc);
-        if (X.qubit(qr, qc) < 0) continue;
-        const int nf = X.face(na, nb);
-        if (nf < 0) continue;
-        const int32_t cand = S.wb[nf] + (e < 2 ? Wt_z : Wt_x);
-        if (cand < cur) {
-          cur = cand;
-          changed = 1;
-        }
+// Ascending bitonic sort across the warp of the values at positions lane (a)
+// and, when N64, lane + 32 (b).
+template <bool N64>
+__device__ __forceinline__ void warp_sort(uint32_t& a, uint32_t& b, int lane) {
+#pragma unroll
+  for (int k = 2; k <= (N64 ? 64 : 32); k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j == 32) {
+        const uint32_t lo = min(a, b), hi = max(a, b);
+        a = lo;
+        b = hi;
+        continue;
       }
-      S.wb[f] = cur;
+      const bool lower = (lane & j) == 0;
+      a = bitonic_step(a, j, lower == ((lane & k) == 0));
+      if (N64) b = bitonic_step(b, j, lower == (((lane + 32) & k) == 0));
     }
-    if (!__syncthreads_or(changed)) break;
   }
+}
 
-  // Defect lists of both colours, in stabilizer-index order.
-  if (warp == 0) {
-    int cnt[2] = {0, 0};
-    for (int base = 0; base < ns; base += 32) {
-      const int f = base + lane;
-      const bool on = f < ns && ((S.syn[f >> 5] >> (f & 31)) & 1);
-      const int c2 = f < ns ? C.face_c2[f] : 0;
-      for (int c = 0; c < 2; ++c) {
-        const uint32_t m = __ballot_sync(0xFFFFFFFFu, on && c2 == c);
-        const int slot = cnt[c] + __popc(m & ((1u << lane) - 1));
-        if (on && c2 == c && XZZX_CHECK(C.err, slot < G::kMaxFaces / 2)) S.defects[c][slot] = (int16_t)f;
-        cnt[c] += __popc(m);
-      }
-    }
-    if (lane == 0) {
-      S.n_def[0] = cnt[0];
-      S.n_def[1] = cnt[1];
+// Candidate list of vertex x (nv <= kListMax vertices), built by one warp.
+// Returns false if a weight does not fit the 26 bits of the sort key.
+template <class G, bool N64>
+__device__ __forceinline__ bool build_list(const Ctx<G>& X, const int16_t* D, int nd, int nv, int x, uint8_t* out,
+                                           int lane) {
+  bool fits = true;
+  uint32_t key[2] = {0xFFFFFFFFu, 0xFFFFFFFFu};
+#pragma unroll
+  for (int h = 0; h < (N64 ? 2 : 1); ++h) {
+    const int y = lane + 32 * h;
+    if (y < nv && y != x) {
+      const int32_t w = pair_weight(X, D, nd, x, y);
+      fits = fits && w >= 0 && w < (1 << 26) - 1;  // keys stay below the 0xFFFFFFFF filler
+      key[h] = ((uint32_t)w << 6) | (uint32_t)y;
     }
   }
-  __syncthreads();
-  if (i >= restarts) return;
+  warp_sort<N64>(key[0], key[1], lane);
+  const uint32_t prev0 = __shfl_up_sync(0xFFFFFFFFu, key[0], 1);
+  const uint32_t last0 = __shfl_sync(0xFFFFFFFFu, key[0], 31);
+  uint32_t prev1 = 0u;
+  if (N64) {
+    const uint32_t up1 = __shfl_up_sync(0xFFFFFFFFu, key[1], 1);
+    prev1 = lane == 0 ? last0 : up1;
+  }
+#pragma unroll
+  for (int h = 0; h < (N64 ? 2 : 1); ++h) {
+    const int pos = lane + 32 * h;
+    const uint32_t k = key[h], pk = h ? prev1 : prev0;
+    if (pos < nv - 1) out[pos] = (uint8_t)((k & 63u) | ((pos > 0 && (k >> 6) == (pk >> 6)) ? 0x80u : 0u));
+  }
+  return __all_sync(0xFFFFFFFFu, fits);
+}
+
+// The reference of restart i of the CTA's shot, by one warp, after the CTA
+// has set up the boundary distances, defect lists and candidate lists.
+template <class G, bool L>
+__device__ __forceinline__ void greedy_restart(const Ctx<G>& X, const DevCode& C, const PhiloxKeys& K, uint64_t shot,
+                                               int i, int mode, uint32_t* __restrict__ init,
+                                               uint8_t* __restrict__ cbits, SharedT<G, L>& S, int warp, int lane) {
+  const int w = C.w;
 
   uint32_t* cfg = S.cfg[warp];
   for (int j = lane; j < 2 * w; j += 32) cfg[j] = 0u;
@@ -286,9 +338,85 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
       partner[x] = -1;
       best[x] = -1;
     }
+    bool listed = false;
+    if constexpr (SharedT<G, L>::kLists) {
+      listed = nv >= 2 && nv <= kListMax && S.lists.usable[colour];
+      if (listed)
+        for (int x = lane; x < nv; x += 32) S.lists.cur[warp][x] = 0;
+    }
     __syncwarp();
     int unmatched = nv;
-    while (unmatched > 0) {
+    while (unmatched > 0 && listed) {
+      if constexpr (SharedT<G, L>::kLists) {
+        // Each free vertex whose best partner was taken walks its sorted list
+        // from its cursor to the first free entry: the lowest weight among
+        // free vertices, and the lowest (u, v) at that weight.  Keys order
+        // the free entries tied at that weight (Alg. 6).
+        for (int x = lane; x < nv; x += 32) {
+          if (partner[x] >= 0) {
+            best[x] = -1;
+            continue;
+          }
+          const int bx = best[x];
+          if (bx >= 0 && partner[bx] < 0) continue;
+          const uint8_t* Lx = S.lists.l[colour][x];
+          int c = S.lists.cur[warp][x];
+          while (c < nv - 1 && partner[Lx[c] & 63] >= 0) ++c;
+          S.lists.cur[warp][x] = (uint8_t)c;
+          if (c >= nv - 1) {  // no free vertex left for x: impossible with an even count
+            best[x] = -1;
+            S.walk_error[warp] = 1;
+            continue;
+          }
+          int bestv = Lx[c] & 63;
+          if (mode == kInitGreedyRandom) {
+            const uint32_t sx = x == nd ? kBoundary : (uint32_t)D[x];
+            const uint32_t s0 = bestv == nd ? kBoundary : (uint32_t)D[bestv];
+            uint32_t bu = min(sx, s0), bvv = max(sx, s0), bkey = 0;
+            bool bkey_ok = false;
+            const uint32_t c3 = kTagGreedy | ((uint32_t)(shot >> 32) << 8);
+            for (int k = c + 1; k < nv - 1; ++k) {
+              const uint32_t ent = Lx[k];
+              if (!(ent & 0x80u)) break;
+              const int y = (int)(ent & 63u);
+              if (partner[y] >= 0) continue;
+              const uint32_t sy = y == nd ? kBoundary : (uint32_t)D[y];
+              const uint32_t u = min(sx, sy), v = max(sx, sy);
+              if (!bkey_ok) {
+                bkey = philox4x32_10(bu | (bvv << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
+                bkey_ok = true;
+              }
+              const uint32_t key = philox4x32_10(u | (v << 16), (uint32_t)i, (uint32_t)shot, c3, K).x;
+              if (key < bkey || (key == bkey && (u < bu || (u == bu && v < bvv)))) {
+                bestv = y;
+                bkey = key;
+                bu = u;
+                bvv = v;
+              }
+            }
+          }
+          best[x] = (int16_t)bestv;
+        }
+        __syncwarp();
+        int made = 0;
+        for (int x = lane; x < nv; x += 32) {
+          const int y = best[x];
+          if (y > x && XZZX_CHECK(C.err, y < nv) && best[y] == x) {
+            partner[x] = (int16_t)y;
+            partner[y] = (int16_t)x;
+            made += 2;
+          }
+        }
+        __syncwarp();
+        for (int off = 16; off > 0; off >>= 1) made += __shfl_xor_sync(0xFFFFFFFFu, made, off);
+        if (made == 0) {
+          if (lane == 0) S.walk_error[warp] = 1;
+          break;
+        }
+        unmatched -= made;
+      }
+    }
+    while (unmatched > 0 && !listed) {
       // Each free vertex finds its best free partner in the order (w, key, u, v),
       // in one pass: a candidate's key is drawn only when its weight ties the
       // best so far.  A best partner that is still free stays the best (removing
@@ -402,6 +530,112 @@ __device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K
     const bool bad = S.walk_error[warp] != 0 || (i == 0 && injected(C.err, XZZX_DEVERR_GREEDY_WALK));
     if (bad) raise_device_error(C.err, XZZX_DEVERR_GREEDY_WALK);
     cbits[i] = (uint8_t)(par_z | (par_x << 1) | (bad ? 0x80 : 0));
+  }
+}
+
+// One CTA: references of restarts [group*kWarps*rpw, (group+1)*kWarps*rpw)
+// of one shot, each warp taking rpw of them in turn, so the CTA's setup serves
+// kWarps*rpw restarts.  syn: the shot's syndrome words; init / cbits: the
+// shot's rows (restarts x 2w words, restarts bytes).
+template <class G, bool L>
+__device__ __forceinline__ void greedy_cta(const DevCode& C, const PhiloxKeys& K, uint64_t shot, int group, int restarts,
+                                           int rpw, int mode, int32_t Wt_x, int32_t Wt_z, const uint32_t* __restrict__ syn,
+                                           uint32_t* __restrict__ init, uint8_t* __restrict__ cbits, SharedT<G, L>& S) {
+  const int d = C.d, ns = C.ns, w = C.w;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  for (int f = tid; f < ns; f += blockDim.x) {
+    S.fa[f] = C.face_a[f];
+    S.fb[f] = C.face_b[f];
+  }
+  for (int j = tid; j < G::at_size(d); j += blockDim.x) S.at[j] = C.face_at[j];
+  for (int j = tid; j < C.sw; j += blockDim.x) S.syn[j] = syn[j];
+  if constexpr (SharedT<G, L>::kLists) {
+    if (tid < 2) S.lists.usable[tid] = 1;
+  }
+  __syncthreads();
+  Ctx<G> X{S, d, w, Wt_x, Wt_z, C.err, C.nq};
+
+  // Boundary distances: start from the boundary edges, relax until stable.
+  for (int f = tid; f < ns; f += blockDim.x) {
+    const int a = S.fa[f], b = S.fb[f];
+    int32_t best = kInf;
+    for (int e = 0; e < 4; ++e) {
+      int na, nb, qr, qc;
+      G::step(a, b, e, na, nb, qr, qc);
+      if (X.qubit(qr, qc) < 0 || X.face(na, nb) >= 0) continue;
+      best = min(best, e < 2 ? Wt_z : Wt_x);
+    }
+    S.wb[f] = best;
+  }
+  __syncthreads();
+  for (int iter = 0; iter < ns + 1; ++iter) {
+    int changed = 0;
+    for (int f = tid; f < ns; f += blockDim.x) {
+      const int a = S.fa[f], b = S.fb[f];
+      int32_t cur = S.wb[f];
+      for (int e = 0; e < 4; ++e) {
+        int na, nb, qr, qc;
+        G::step(a, b, e, na, nb, qr, qc);
+        if (X.qubit(qr, qc) < 0) continue;
+        const int nf = X.face(na, nb);
+        if (nf < 0) continue;
+        const int32_t cand = S.wb[nf] + (e < 2 ? Wt_z : Wt_x);
+        if (cand < cur) {
+          cur = cand;
+          changed = 1;
+        }
+      }
+      S.wb[f] = cur;
+    }
+    if (!__syncthreads_or(changed)) break;
+  }
+
+  // Defect lists of both colours, in stabilizer-index order.
+  if (warp == 0) {
+    int cnt[2] = {0, 0};
+    for (int base = 0; base < ns; base += 32) {
+      const int f = base + lane;
+      const bool on = f < ns && ((S.syn[f >> 5] >> (f & 31)) & 1);
+      const int c2 = f < ns ? C.face_c2[f] : 0;
+      for (int c = 0; c < 2; ++c) {
+        const uint32_t m = __ballot_sync(0xFFFFFFFFu, on && c2 == c);
+        const int slot = cnt[c] + __popc(m & ((1u << lane) - 1));
+        if (on && c2 == c && XZZX_CHECK(C.err, slot < G::kMaxFaces / 2)) S.defects[c][slot] = (int16_t)f;
+        cnt[c] += __popc(m);
+      }
+    }
+    if (lane == 0) {
+      S.n_def[0] = cnt[0];
+      S.n_def[1] = cnt[1];
+    }
+  }
+  __syncthreads();
+  if constexpr (SharedT<G, L>::kLists) {
+    // Candidate lists of both colours, every warp of the CTA building some.
+    if (mode != kInitBoundary) {
+      for (int colour = 0; colour < 2; ++colour) {
+        const int nd = S.n_def[colour], nv = nd + (nd & 1);
+        if (nv < 2 || nv > kListMax) continue;
+        bool fits = true;
+        for (int x = warp; x < nv; x += kWarps)
+          fits = (nv > 32 ? build_list<G, true>(X, S.defects[colour], nd, nv, x, S.lists.l[colour][x], lane)
+                          : build_list<G, false>(X, S.defects[colour], nd, nv, x, S.lists.l[colour][x], lane)) && fits;
+        if (lane == 0 && !fits) S.lists.usable[colour] = 0;
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (SharedT<G, L>::kLists) {
+    for (int r = 0; r < rpw; ++r) {
+      const int i = (group * rpw + r) * kWarps + warp;
+      if (i >= restarts) break;
+      __syncwarp();  // the warp's previous reference is written out
+      greedy_restart<G, L>(X, C, K, shot, i, mode, init, cbits, S, warp, lane);
+    }
+  } else {  // one restart per warp (rpw is 1 without lists)
+    const int i = group * kWarps + warp;
+    if (i < restarts) greedy_restart<G, L>(X, C, K, shot, i, mode, init, cbits, S, warp, lane);
   }
 }
 

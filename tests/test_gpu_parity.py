@@ -320,3 +320,47 @@ def test_partition_independence(X, torch):
     torch.cuda.synchronize()
     for key in ("cls", "E4", "recovery", "best_cfg", "fail"):
         assert torch.equal(whole[key], torch.cat([a[key], b[key]])), key
+
+
+@pytest.mark.parametrize("d,density,equal_weights", [(15, 0.5, False), (15, 0.6, False), (11, 0.5, True),
+                                                     (15, 0.5, True)])
+def test_greedy_parity_candidate_list_sizes(X, torch, d, density, equal_weights):
+    """Colours just under and just over 64 vertices (the candidate-list path
+    with its 64-wide sort, and the full scan), with equal X and Z weights so
+    that many pairs tie and the random keys decide."""
+    from inputs import random_syndromes
+    code = X.Code(d)
+    noise = X.make_noise(0.05, 0.05, 0.05) if equal_weights else X.make_noise(0.03, 0.05, 0.09)
+    pxyz = oracle_noise(noise)
+    osyn = random_syndromes(d * d - 1, 4, density, seed=100 + d)
+    syn = gpu_words(torch, syn_bits_to_words(osyn))
+    for randomised in (0, 1):
+        init, cbits = X.greedy_init(code, noise, 9, 3, syn, 3, randomised=randomised)
+        torch.cuda.synchronize()
+        init = to_np(init)
+        for s in range(4):
+            for i in range(3):
+                ref, _ = O.greedy(d, pxyz, noise.scale, 9, 3 + s, i, randomised, osyn[s])
+                assert np.array_equal(words_to_labels(init[s, i], d * d), ref), (s, i, randomised)
+
+
+@pytest.mark.parametrize("d,R,n", [(11, 64, 1024), (11, 64, 600), (7, 16, 4096)])
+def test_greedy_restarts_per_warp_identical(X, torch, d, R, n):
+    """A launch large enough that each greedy warp takes several restarts in
+    turn (4 or 2) gives the references of small launches (one restart per
+    warp), bit for bit, and sampled references equal the oracle."""
+    code = X.Code(d)
+    noise = X.noise_from_eta(0.16, 100.0)
+    pxyz = oracle_noise(noise)
+    err, syn = X.sample_errors(code, noise, 21, 0, n)
+    big, big_cb = X.greedy_init(code, noise, 21, 0, syn, R)
+    parts = [X.greedy_init(code, noise, 21, s0, syn[s0:s0 + 128], R) for s0 in range(0, n, 128)]
+    torch.cuda.synchronize()
+    assert torch.equal(big, torch.cat([p[0] for p in parts]))
+    assert torch.equal(big_cb, torch.cat([p[1] for p in parts]))
+    osyn = syn_words_to_bits(to_np(syn), d * d - 1)
+    big = to_np(big)
+    for s in (0, n // 2, n - 1):
+        for i in (0, R // 2 + 1, R - 1):
+            ref, _ = O.greedy(d, pxyz, noise.scale, 21, s, i, 1, osyn[s])
+            assert np.array_equal(words_to_labels(big[s, i], d * d), ref), (s, i)
