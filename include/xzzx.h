@@ -308,7 +308,7 @@ typedef struct {
 
 typedef struct {
   int32_t n_segments, n_chunks, n_distances, persistent_grid;
-  int32_t launches_batched, launches_plain;
+  int32_t launches_batched, launches_plain; /* kernel launches of modes 0 and 1 */
   size_t workspace_bytes;
   double move_attempts;  /* per run */
   int64_t total_shots;
@@ -327,9 +327,10 @@ typedef struct xzzx_batch xzzx_batch;
  * draw; cfg may be NULL. */
 xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t seed, const xzzx_batch_cfg* cfg,
                               xzzx_batch** out);
-/* Decode every segment on the stream.  mode 0: one greedy launch, one
- * persistent annealing launch whose CTAs pull chunks (longest first) from an
- * atomic counter, one decision launch.  mode 1: the three kernels once per
+/* Decode every segment on the stream.  mode 0: one greedy launch (two when
+ * the batch has distances both up to 15 and above), one persistent annealing
+ * launch whose CTAs pull chunks (longest first) from an atomic counter, one
+ * decision launch.  mode 1: the three kernels once per
  * distance (the plain form).  mode 2: as mode 1 with one warp per chain
  * (xzzx_anneal_warp).  mode 3: one greedy launch, then each distance's own
  * annealing kernel on its own stream forked from this one (largest distance

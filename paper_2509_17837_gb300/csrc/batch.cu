@@ -672,7 +672,8 @@ xzzx_status xzzx_batch_get_info(const xzzx_batch* b, xzzx_batch_info* out) {
   out->n_chunks = (int)b->plan.lpt.size();
   out->n_distances = (int)b->plan.ranges.size();
   out->persistent_grid = std::min(b->grid, std::max((int)b->plan.lpt.size(), 1));
-  out->launches_batched = 3;
+  // Mode 0: greedy (one launch per side of d = 15 present), the persistent anneal, the decision.
+  out->launches_batched = 2 + (b->plan.list_cta_end > 0 ? 1 : 0) + (b->plan.list_cta_end < b->plan.total_ctas ? 1 : 0);
   out->n_classes = (int)b->plan.classes.size();
   out->launches_plain = 3 * (int)b->plan.ranges.size();
   out->workspace_bytes = b->plan.workspace_bytes;
