@@ -184,3 +184,26 @@ def test_batch_warp_mapping_occupancy_cap(env, cap):
     assert_same(b.outputs, refs)
     free.close()
     b.close()
+
+
+def test_batch_restarts_per_warp_match_per_segment_calls(env):
+    """A batch large enough that its greedy launch gives each warp four
+    restarts (segments d <= 15) decodes exactly as per-segment calls, whose
+    own launches take two or one restarts per warp."""
+    X, torch = env
+    seed = 0x4E57
+    specs = [(5, 0.12, 10, 16, 3000), (11, 0.16, 100, 64, 500), (17, 0.15, 100, 8, 200)]
+    segs = []
+    for d, p, eta, R, n in specs:
+        code = X.Code(d)
+        noise = X.noise_from_eta(p, eta)
+        sched = X.Schedule(noise, 12, 0.05, 20.0)
+        err, syn = X.sample_errors(code, noise, seed, 0, n)
+        segs.append(dict(code=code, noise=noise, sched=sched, shot0=0, syndromes=syn, restarts=R, true_errors=err))
+    refs = reference_outputs(X, torch, segs, seed)
+    b = X.Batch(segs, seed)
+    for mode in (0, 1):
+        b.run(mode)
+        torch.cuda.synchronize()
+        assert_same(b.outputs, refs)
+    b.close()

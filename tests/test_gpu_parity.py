@@ -344,11 +344,12 @@ def test_greedy_parity_candidate_list_sizes(X, torch, d, density, equal_weights)
                 assert np.array_equal(words_to_labels(init[s, i], d * d), ref), (s, i, randomised)
 
 
-@pytest.mark.parametrize("d,R,n", [(11, 64, 1024), (11, 64, 600), (7, 16, 4096)])
+@pytest.mark.parametrize("d,R,n", [(11, 64, 1024), (11, 64, 600), (7, 16, 4096), (9, 37, 1400)])
 def test_greedy_restarts_per_warp_identical(X, torch, d, R, n):
     """A launch large enough that each greedy warp takes several restarts in
-    turn (4 or 2) gives the references of small launches (one restart per
-    warp), bit for bit, and sampled references equal the oracle."""
+    turn (4 or 2; with 37 restarts the last group of each shot is partial)
+    gives the references of small launches (one restart per warp), bit for
+    bit, and sampled references equal the oracle."""
     code = X.Code(d)
     noise = X.noise_from_eta(0.16, 100.0)
     pxyz = oracle_noise(noise)
