@@ -45,6 +45,12 @@ ANNEAL_MEASURED = {"inst_per_attempt": 20.51, "alu_inst_per_attempt": ANNEAL_ALU
                    "shared_bank_conflicts_per_wavefront": 1.2654e10 / 2.0863e10,
                    "source": "ncu capture of one anneal_kernel<11> launch of 4000 shots, "
                              "profiles/anneal_d11_ncu_full.md"}
+# The same counters for the d=31 row kernel of the large workload.
+ANNEAL_D31_DRAM_BYTES_PER_CHAIN = 4.580864e6 / (57 * 1024)
+ANNEAL_D31_MEASURED = {"inst_per_attempt": 18.83, "alu_inst_per_attempt": 11.69,
+                       "shared_bank_conflicts_per_wavefront": 5.7998e10 / 9.3272e10,
+                       "source": "ncu capture of one anneal_kernel_rows<31> launch of 57 shots, "
+                                 "profiles/anneal_d31_ncu_full.md"}
 
 
 def workload_config(shots_per_p, world):
@@ -654,8 +660,9 @@ def run_large(args):
         "shots_per_s": shots / (ms / 1e3), "shots_timed": shots * args.steps,
         "logical_error_rates": [stats.ler_record(p, f, S * args.steps) for p, f in zip(LARGE_PS, fails)],
         "chain_mapping": mapping, "occupancy_sweep": occupancy, "clocks": clocks,
-        "roofline": roofline_record(att, clocks, props.multi_processor_count, traffic=None,
-                                    kernel="anneal_kernel_rows<31>")}))
+        "roofline": roofline_record(att, clocks, props.multi_processor_count,
+                                    traffic=ANNEAL_D31_DRAM_BYTES_PER_CHAIN * S * R * 4,
+                                    kernel="anneal_kernel_rows<31>", measured_per_attempt=ANNEAL_D31_MEASURED)}))
 
 
 # --------------------------------------------------------------------------- logical error rate curves
