@@ -45,12 +45,15 @@ ANNEAL_MEASURED = {"inst_per_attempt": 20.51, "alu_inst_per_attempt": ANNEAL_ALU
                    "shared_bank_conflicts_per_wavefront": 1.2654e10 / 2.0863e10,
                    "source": "ncu capture of one anneal_kernel<11> launch of 4000 shots, "
                              "profiles/anneal_d11_ncu_full.md"}
-# The same counters for the d=31 row kernel of the large workload.
-ANNEAL_D31_DRAM_BYTES_PER_CHAIN = 4.580864e6 / (57 * 1024)
+# The same counters for the d=31 row kernel of the large workload, taken on
+# its form before the group-by-group columns and the 128-register bound:
+# DRAM traffic is therefore not reported for the current kernel.
+ANNEAL_D31_DRAM_BYTES_PER_CHAIN = None
 ANNEAL_D31_MEASURED = {"inst_per_attempt": 18.83, "alu_inst_per_attempt": 11.69,
                        "shared_bank_conflicts_per_wavefront": 5.7998e10 / 9.3272e10,
-                       "source": "ncu capture of one anneal_kernel_rows<31> launch of 57 shots, "
-                                 "profiles/anneal_d31_ncu_full.md"}
+                       "dram_bytes_per_chain": 4.580864e6 / (57 * 1024),
+                       "source": "ncu capture of one launch of the previous form of the d=31 row kernel "
+                                 "(158 registers, 3 CTAs per SM), profiles/anneal_d31_ncu_full.md"}
 
 
 def workload_config(shots_per_p, world):
@@ -661,8 +664,9 @@ def run_large(args):
         "logical_error_rates": [stats.ler_record(p, f, S * args.steps) for p, f in zip(LARGE_PS, fails)],
         "chain_mapping": mapping, "occupancy_sweep": occupancy, "clocks": clocks,
         "roofline": roofline_record(att, clocks, props.multi_processor_count,
-                                    traffic=ANNEAL_D31_DRAM_BYTES_PER_CHAIN * S * R * 4,
-                                    kernel="anneal_kernel_rows<31>", measured_per_attempt=ANNEAL_D31_MEASURED)}))
+                                    traffic=(None if ANNEAL_D31_DRAM_BYTES_PER_CHAIN is None
+                                             else ANNEAL_D31_DRAM_BYTES_PER_CHAIN * S * R * 4),
+                                    kernel="anneal_kernel_rows4<31>", measured_per_attempt=ANNEAL_D31_MEASURED)}))
 
 
 # --------------------------------------------------------------------------- logical error rate curves
@@ -759,7 +763,7 @@ def main():
     ap.add_argument("--workload", default="d11", choices=["d11", "uneven", "serve", "large", "ler"])
     ap.add_argument("--ler-shots", type=int, default=100000)
     ap.add_argument("--layout", default="rotated", choices=["rotated", "planar"])
-    ap.add_argument("--large-shots-per-p", type=int, default=57)
+    ap.add_argument("--large-shots-per-p", type=int, default=76)  # one wave: 152 SMs x 4 CTAs x 128 chains
     ap.add_argument("--no-occupancy-sweep", action="store_true")
     ap.add_argument("--uneven-shots", type=int, default=1000000)
     ap.add_argument("--serve-seconds", type=float, default=1.0)

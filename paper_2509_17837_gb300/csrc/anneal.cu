@@ -60,9 +60,17 @@ template <int D>
 __global__ void __launch_bounds__(Shape<D>::kThreads) anneal_kernel_rows(const __grid_constant__ AnnealArgs A) {
   anneal_body<D>(A);
 }
+// d >= 29: held to 128 registers, four CTAs per SM instead of three (the
+// compiler's own choice is about 158); more chains in flight hide the sweep's
+// dependent integer chain better than the extra registers do.
+template <int D>
+__global__ void __launch_bounds__(Shape<D>::kThreads, 4) anneal_kernel_rows4(const __grid_constant__ AnnealArgs A) {
+  anneal_body<D>(A);
+}
 template <int D>
 constexpr auto anneal_kernel_of() {
   if constexpr (D <= kPairMaxD) return &anneal_kernel<D>;
+  else if constexpr (D >= 29) return &anneal_kernel_rows4<D>;
   else return &anneal_kernel_rows<D>;
 }
 

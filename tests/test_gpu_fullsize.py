@@ -4,7 +4,7 @@ The d = 11 workload runs one launch of 20,000 shots x 64 restarts (256 chains
 per shot, 1000 sweeps) exactly as a benchmark step does, and a sample of its
 shots is decoded by the oracle one by one: classes, coset energies, every
 chain's minimum energy, recoveries and failure flags must agree bit for bit.
-The d = 31 workload (256 restarts, 1e4 sweeps, one launch of 57 shots) is too
+The d = 31 workload (256 restarts, 1e4 sweeps, one launch of 76 shots) is too
 large for the oracle to decode a whole shot, so sampled references and chains
 are checked one by one and the decision is checked against the GPU's own chain
 energies (the coset minima follow from them by Eq. coset_correspondence).
@@ -66,7 +66,7 @@ def test_d11_bench_launch_sampled_shots(X, torch):
 def test_d31_bench_launch_sampled_chains(X, torch):
     import bench
     d, R, N, b0, b1, scale, eta, seed = 31, 256, 10000, 0.02, 30.0, 4096, 1000.0, 0xD31
-    S, p = 57, bench.LARGE_PS[0]
+    S, p = 76, bench.LARGE_PS[0]
     code = X.Code(d)
     noise = X.noise_from_eta(p, eta, 0, scale)
     sched = X.Schedule(noise, N, b0, b1)

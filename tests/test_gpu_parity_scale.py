@@ -12,7 +12,7 @@ failure flags must agree bit for bit
 sample size.
 
 d = 31 workload (eta = 1000, 256 restarts, 1e4 sweeps, scale 4096): one
-launch of 57 shots per noise point, for three noise points; 64 sampled
+launch of 76 shots per noise point, for three noise points; 64 sampled
 (shot, restart, coset) chains per point are re-annealed by the oracle from
 its own greedy references, which must equal the GPU's references bit for bit.
 """
@@ -91,7 +91,7 @@ def test_d11_parity_sampled_shots_every_p(X, torch):
 def test_d31_parity_sampled_chains_three_p(X, torch):
     import bench
     d, R, N, b0, b1, scale, eta, seed = 31, 256, 10000, 0.02, 30.0, 4096, 1000.0, 0xD31
-    S = 57
+    S = 76
     code = X.Code(d)
     for p in (bench.LARGE_PS[0], bench.LARGE_PS[len(bench.LARGE_PS) // 2], bench.LARGE_PS[-1]):
         noise = X.noise_from_eta(p, eta, 0, scale)
