@@ -328,7 +328,7 @@ typedef struct xzzx_batch xzzx_batch;
 xzzx_status xzzx_batch_create(const xzzx_segment* segs, int n_segs, uint64_t seed, const xzzx_batch_cfg* cfg,
                               xzzx_batch** out);
 /* Decode every segment on the stream.  mode 0: one greedy launch (two when
- * the batch has distances both up to 15 and above), one persistent annealing
+ * the batch has distances both up to 17 and above), one persistent annealing
  * launch whose CTAs pull chunks (longest first) from an atomic counter, one
  * decision launch.  mode 1: the three kernels once per
  * distance (the plain form).  mode 2: as mode 1 with one warp per chain

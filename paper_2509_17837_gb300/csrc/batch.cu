@@ -160,7 +160,7 @@ xzzx_status run_greedy(const Plan& p, const PlanDev& d, const PhiloxKeys& K, int
   G.segs = d.segs;
   G.cta_prefix = d.cta_prefix;
   G.n_segs = (int)p.segs.size();
-  // Segments are ordered by distance: CTAs before list_cta_end (d <= 15) run
+  // Segments are ordered by distance: CTAs before list_cta_end (d <= 17) run
   // the kernel with candidate lists, the rest the one without.
   const int64_t end = cta0 + n_ctas, split = std::min(std::max(p.list_cta_end, cta0), end);
   if (split > cta0) {

@@ -81,7 +81,7 @@ struct Plan {
   int dmax = 0;
   double attempts = 0;
   int64_t total_shots = 0, total_ctas = 0;
-  int64_t list_cta_end = 0;  // greedy CTAs [0, list_cta_end) are of segments with d <= 15
+  int64_t list_cta_end = 0;  // greedy CTAs [0, list_cta_end) are of segments with d <= 17
   size_t workspace_bytes = 0;
 };
 

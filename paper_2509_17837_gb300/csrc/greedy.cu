@@ -41,7 +41,7 @@ xzzx_status launch_greedy(const xzzx_code* code, const xzzx_noise* noise, uint64
   A.n_shots = n_shots;
   A.restarts = restarts;
   A.randomised = randomised;
-  A.rpw = 1;  // several restarts per warp only with candidate lists (d <= 15)
+  A.rpw = 1;  // several restarts per warp only with candidate lists (d <= 17)
   for (int r = kMaxRestartsPerWarp; r > 1 && code->layout != kLayoutPlanar && code->d <= kListMaxD; r >>= 1)
     if ((int64_t)n_shots * greedy_groups(restarts, r) >= kMinGreedyCtas) {
       A.rpw = r;

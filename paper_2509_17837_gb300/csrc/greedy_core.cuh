@@ -1,11 +1,11 @@
 // Randomised greedy matching (Algs. 5 and 6) on the GPU.
 //
 // One CTA per (shot, group of kWarps*rpw restarts); each warp takes rpw
-// restarts in turn (for d <= 15 rpw = 4, 2 or 1, the most that still leaves
+// restarts in turn (for d <= 17 rpw = 4, 2 or 1, the most that still leaves
 // the launch several waves of CTAs; 1 above).  The CTA first computes, in
 // shared memory, each face's shortest distance to the open boundary of its
 // decoding graph (w(u,b) of Eq. distance_u_boundary) by Bellman-Ford
-// relaxation, and the defect list of each decoding-graph colour; for d <= 15,
+// relaxation, and the defect list of each decoding-graph colour; for d <= 17,
 // also every vertex's candidate list (below).  All of it depends on the shot
 // only, so it serves every restart of the CTA.
 //
@@ -43,7 +43,7 @@ constexpr int kWarps = 4;
 // A launch with candidate lists takes the largest restarts-per-warp count (4,
 // 2 or 1) that still gives it this many CTAs (several waves on a 152-SM GPU):
 // large launches then share each CTA's setup across more restarts, small ones
-// keep their CTAs.  Without lists (d > 15) a warp takes one restart: the scan
+// keep their CTAs.  Without lists (d > 17) a warp takes one restart: the scan
 // dominates there, and longer CTAs only lengthen the launch's tail.
 constexpr int64_t kMinGreedyCtas = 4096;
 constexpr int kMaxRestartsPerWarp = 4;
@@ -132,10 +132,11 @@ struct CandidateLists {
 };
 struct NoLists {};
 
-// Largest distance whose greedy launches carry candidate lists.  Past it most
-// colours hold more than kListMax vertices at the noise of interest, and the
-// lists' shared memory would only lower the occupancy of the scan that runs.
-constexpr int kListMaxD = 15;
+// Largest distance whose greedy launches carry candidate lists.  At d = 17
+// colours still fit kListMax vertices for p up to about 0.2 (2-3x faster
+// references); past it most colours hold more, and the lists' shared memory
+// would only lower the occupancy of the scan that runs.
+constexpr int kListMaxD = 17;
 
 template <class G>
 struct SharedBase {

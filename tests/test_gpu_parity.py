@@ -54,7 +54,7 @@ def oracle_noise(noise):
 
 
 @pytest.mark.parametrize("d,p,eta,n,R", [(3, 0.1, 10, 64, 8), (5, 0.2, 3, 40, 6), (11, 0.22, 100, 30, 9),
-                                         (21, 0.2, 100, 6, 5), (31, 0.3, 1000, 3, 4)])
+                                         (17, 0.18, 100, 8, 5), (21, 0.2, 100, 6, 5), (31, 0.3, 1000, 3, 4)])
 @pytest.mark.parametrize("randomised", [1, 0, 2])   # Alg. 6, Alg. 5, boundary initializer
 def test_greedy_parity(X, torch, d, p, eta, n, R, randomised):
     code = X.Code(d)
