@@ -75,6 +75,13 @@ const char* xzzx_last_error(void);
 /* Library version string. */
 const char* xzzx_version(void);
 
+/* Size in bytes of public struct number which, as compiled into the library:
+ * 0 xzzx_noise, 1 xzzx_code_info, 2 xzzx_segment, 3 xzzx_batch_cfg,
+ * 4 xzzx_batch_info, 5 xzzx_serve_cfg, 6 xzzx_result, 7 xzzx_serve_stats;
+ * 0 for any other number.  Host only (no device needed), for bindings to
+ * check their own copies of the layouts.  The paper has no counterpart. */
+size_t xzzx_abi_struct_size(int which);
+
 /* ------------------------------------------------------------------------ */
 /* Code tables (Sec. "The XZZX code", Eq. stabilizer_generator).           */
 /* ------------------------------------------------------------------------ */

@@ -83,6 +83,7 @@ SIGNATURES = {
     "xzzx_device_errors": ([_p, _p, _p, _i, _p], _i),
     "xzzx_debug_inject": ([_p, C.c_uint32, _p], _i),
     "xzzx_version": ([], C.c_char_p),
+    "xzzx_abi_struct_size": ([_i], C.c_size_t),
     "xzzx_make_code": ([_i, _i, C.POINTER(_p)], _i),
     "xzzx_get_code_info": ([_p, C.POINTER(CodeInfo)], _i),
     "xzzx_free_code": ([_p], None),

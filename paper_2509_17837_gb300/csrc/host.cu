@@ -114,6 +114,20 @@ const char* xzzx_last_error(void) { return g_last_error.c_str(); }
 
 const char* xzzx_version(void) { return "xzzx-gb300 0.1 (sm_103a)"; }
 
+size_t xzzx_abi_struct_size(int which) {
+  switch (which) {
+    case 0: return sizeof(xzzx_noise);
+    case 1: return sizeof(xzzx_code_info);
+    case 2: return sizeof(xzzx_segment);
+    case 3: return sizeof(xzzx_batch_cfg);
+    case 4: return sizeof(xzzx_batch_info);
+    case 5: return sizeof(xzzx_serve_cfg);
+    case 6: return sizeof(xzzx_result);
+    case 7: return sizeof(xzzx_serve_stats);
+    default: return 0;
+  }
+}
+
 namespace xzzx {
 namespace {
 

@@ -38,6 +38,17 @@ def test_exports_every_declared_symbol(X):
     assert set(SIGNATURES) == set(names)
 
 
+def test_ctypes_struct_layouts_match_the_library(X):
+    """The binding's ctypes copies of the public structs have the sizes the
+    library was compiled with (a field added on one side only fails here)."""
+    from paper_2509_17837_gb300 import _lib as L
+    mirrors = [L.Noise, L.CodeInfo, L.Segment, L.BatchCfg, L.BatchInfo, L.ServeCfg, L.Result, L.ServeStats]
+    for which, cls in enumerate(mirrors):
+        assert L.lib().xzzx_abi_struct_size(which) == ctypes.sizeof(cls), cls.__name__
+    assert L.lib().xzzx_abi_struct_size(len(mirrors)) == 0
+    assert L.lib().xzzx_abi_struct_size(-1) == 0
+
+
 def test_argument_validation(X):
     from paper_2509_17837_gb300._lib import XZZX_EINVAL, XZZX_EUNSUPPORTED, XzzxError
     for d in (1, 2, 4, 33, 0, -3):
